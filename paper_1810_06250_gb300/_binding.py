@@ -1,0 +1,219 @@
+"""ctypes binding of include/rms.h -- argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does
+nothing but convert arguments (torch tensors -> device pointers, numpy arrays
+-> host pointers, the current torch stream -> cudaStream_t) and turn a
+non-zero rms_status into an RmsError.  All arithmetic happens in librms.so.
+There is no fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librms.so")
+
+RMS_OK, RMS_ERR_INVALID_ARG, RMS_ERR_OOM, RMS_ERR_CUDA, RMS_ERR_UNSUPPORTED, RMS_ERR_TIMEOUT = range(6)
+RMS_AXIS_LAMBDA2, RMS_AXIS_FREQ_HZ = 0, 1
+RMS_CHAN_MAJOR, RMS_LOS_MAJOR = 0, 1
+RMS_FP32_SIMT_FLY, RMS_FP32_SIMT_TABLE, RMS_BF16, RMS_BF16X3, RMS_FP16X3 = range(5)
+(RMS_INFO_NCHAN, RMS_INFO_NCHAN_ACTIVE, RMS_INFO_NPHI, RMS_INFO_PRECISION, RMS_INFO_KPAD,
+ RMS_INFO_NPAD, RMS_INFO_TILE_N, RMS_INFO_DEVICE) = range(8)
+RMS_GET_LAMBDA2, RMS_GET_ACTIVE, RMS_GET_TABLE, RMS_GET_B_HI, RMS_GET_B_LO, RMS_GET_RMSF64 = range(6)
+
+PRECISIONS = {"fp32_fly": RMS_FP32_SIMT_FLY, "fp32_table": RMS_FP32_SIMT_TABLE, "bf16": RMS_BF16,
+              "bf16x3": RMS_BF16X3, "fp16x3": RMS_FP16X3}
+LAYOUTS = {"chan": RMS_CHAN_MAJOR, "los": RMS_LOS_MAJOR}
+
+# Every symbol include/rms.h declares (checked by the ABI test).
+EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_plan_sync",
+           "rms_plan_info", "rms_plan_get", "rms_plan_destroy", "rms_status_string",
+           "rms_plan_set_timeout")
+
+
+class RmsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, rms_status_string(status), status))
+
+
+_lock = threading.Lock()
+_lib = None
+_c_void_p = ctypes.c_void_p
+_i32, _i64 = ctypes.c_int32, ctypes.c_int64
+
+
+def load(path: str = LIB_PATH):
+    """Load librms.so (once).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("librms.so is not built (%s); run paper_1810_06250_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        P = _c_void_p
+        sig = {
+            "rms_plan_create": [ctypes.POINTER(P), P, _i32, _i32, P, P, _i32, _i32, _i32],
+            "rms_rmsf": [P, P, P, P, P, P],
+            "rms_synth": [P, P, P, _i64, _i32, P, P, P, P, P],
+            "rms_synth_host": [P, P, P, _i64, _i32, P, P, P, P, P],
+            "rms_plan_sync": [P, P],
+            "rms_plan_info": [P, _i32, P],
+            "rms_plan_get": [P, _i32, P, _i64],
+            "rms_plan_destroy": [P],
+            "rms_plan_set_timeout": [P, _i64],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.rms_status_string.argtypes = [ctypes.c_int]
+        lib.rms_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(st: int, where: str):
+    if st != RMS_OK:
+        raise RmsError(st, where)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    return t.data_ptr()
+
+
+def _hptr(a, dtype=None, name="array"):
+    """Host pointer of a tensor/ndarray in CPU memory (or None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("%s must be a contiguous CPU tensor" % name)
+        if dtype is not None and str(a.dtype) != "torch." + dtype:
+            raise ValueError("%s must have dtype %s" % (name, dtype))
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("%s must be C-contiguous" % name)
+    if dtype is not None and a.dtype != np.dtype(dtype):
+        raise ValueError("%s must have dtype %s" % (name, dtype))
+    return a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def rms_status_string(status: int) -> str:
+    return load().rms_status_string(int(status)).decode()
+
+
+def rms_plan_create(axis, weights, phi, precision, axis_kind=RMS_AXIS_FREQ_HZ, device=0) -> int:
+    """Returns the opaque plan handle (an int).  See include/rms.h."""
+    lib = load()
+    axis = np.ascontiguousarray(axis, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    out = _c_void_p()
+    st = lib.rms_plan_create(ctypes.byref(out), axis.ctypes.data, axis.shape[0], int(axis_kind),
+                             None if w is None else w.ctypes.data, phi.ctypes.data, phi.shape[0],
+                             int(precision), int(device))
+    _check(st, "rms_plan_create")
+    return out.value
+
+
+def rms_plan_destroy(plan: int):
+    _check(load().rms_plan_destroy(plan), "rms_plan_destroy")
+
+
+def rms_rmsf(plan: int, R_out=None):
+    """Returns (lambda0sq, K, fwhm_meas, fwhm_est); fills R_out (CUDA float32 [2*nphi]) if given."""
+    lib = load()
+    vals = [ctypes.c_double() for _ in range(4)]
+    st = lib.rms_rmsf(plan, _dptr(R_out, None, "R_out"), *[ctypes.byref(v) for v in vals])
+    _check(st, "rms_rmsf")
+    return tuple(v.value for v in vals)
+
+
+def _layout(layout):
+    return LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+
+
+def rms_synth(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None, peak_abs=None,
+              phi_peak=None, stream=None):
+    """Asynchronous synthesis on CUDA tensors (see include/rms.h)."""
+    import torch
+    st = load().rms_synth(plan, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                          _layout(layout), _dptr(F_out, None, "F_out"),
+                          _dptr(peak_idx, torch.int32, "peak_idx"), _dptr(peak_abs, torch.float32, "peak_abs"),
+                          _dptr(phi_peak, torch.float32, "phi_peak"), _stream(stream))
+    _check(st, "rms_synth")
+
+
+def rms_synth_host(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None, peak_abs=None,
+                   phi_peak=None, stream=None):
+    """Synthesis from host buffers (numpy arrays or CPU tensors, pinned for speed); synchronous."""
+    st = load().rms_synth_host(plan, _hptr(Q, "float32", "Q"), _hptr(U, "float32", "U"), int(nlos),
+                               _layout(layout), _hptr(F_out, None, "F_out"), _hptr(peak_idx, "int32", "peak_idx"),
+                               _hptr(peak_abs, "float32", "peak_abs"), _hptr(phi_peak, "float32", "phi_peak"),
+                               _stream(stream))
+    _check(st, "rms_synth_host")
+
+
+def rms_plan_sync(plan: int, stream=None):
+    _check(load().rms_plan_sync(plan, _stream(stream)), "rms_plan_sync")
+
+
+def rms_plan_set_timeout(plan: int, ns: int):
+    _check(load().rms_plan_set_timeout(plan, int(ns)), "rms_plan_set_timeout")
+
+
+def rms_plan_info(plan: int, what: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().rms_plan_info(plan, int(what), ctypes.byref(v)), "rms_plan_info")
+    return v.value
+
+
+def rms_plan_get(plan: int, what: int) -> np.ndarray:
+    """Copy a plan-owned array to a new numpy array (shapes as in include/rms.h)."""
+    nchan = rms_plan_info(plan, RMS_INFO_NCHAN)
+    nact = rms_plan_info(plan, RMS_INFO_NCHAN_ACTIVE)
+    nphi = rms_plan_info(plan, RMS_INFO_NPHI)
+    kpad = rms_plan_info(plan, RMS_INFO_KPAD)
+    npad = rms_plan_info(plan, RMS_INFO_NPAD)
+    shapes = {
+        RMS_GET_LAMBDA2: ((nchan,), np.float64),
+        RMS_GET_ACTIVE: ((nact,), np.int32),
+        RMS_GET_TABLE: ((nact, nphi, 2), np.float32),
+        RMS_GET_B_HI: ((npad, kpad), np.uint16),
+        RMS_GET_B_LO: ((npad, kpad), np.uint16),
+        RMS_GET_RMSF64: ((nphi, 2), np.float64),
+    }
+    shape, dt = shapes[what]
+    out = np.empty(shape, dtype=dt)
+    _check(load().rms_plan_get(plan, int(what), out.ctypes.data, out.nbytes), "rms_plan_get")
+    return out

@@ -1,0 +1,483 @@
+// C ABI of the RM-synthesis library: plan creation, RMSF, synthesis dispatch,
+// host-buffer synthesis, sticky device errors.  See include/rms.h for the
+// contract of every entry point.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "rms_internal.h"
+
+namespace {
+
+constexpr double kCLight = 299792458.0;   // m/s, exact
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+rms_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return RMS_OK;
+    if (e == cudaErrorMemoryAllocation) return RMS_ERR_OOM;
+    return RMS_ERR_CUDA;
+}
+
+bool is_tensor(int prec) { return prec == RMS_BF16 || prec == RMS_BF16X3 || prec == RMS_FP16X3; }
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+void free_plan(rms_plan_s *p)
+{
+    if (!p) return;
+    cudaFree(p->d_active);
+    cudaFree(p->d_dl2);
+    cudaFree(p->d_wact);
+    cudaFree(p->d_phi);
+    cudaFree(p->d_phi32);
+    cudaFree(p->d_l2x32);
+    cudaFree(p->d_w32);
+    cudaFree(p->d_table);
+    cudaFree(p->d_bhi);
+    cudaFree(p->d_blo);
+    cudaFree(p->d_R64);
+    cudaFree(p->d_stage);
+    cudaFree(p->d_rexp);
+    if (p->h_err) cudaFreeHost(p->h_err);
+    delete p;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+bool encode_b_map(CUtensorMap *map, void *base, int kpad, int npad, int tile_n)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)npad};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kKBlock, (cuuint32_t)tile_n};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// FWHM of |R|'s main lobe: |R| is even in phi, so find the first phi > 0 where
+// |R(phi)| <= 1/2 by evaluating R on 1024-point grids on the device, three
+// rounds of bracketing, then linear interpolation inside the last bracket.
+double measure_fwhm(rms_plan_s *p)
+{
+    const int n = 1024;
+    double *d_phi = nullptr, *d_R = nullptr;
+    if (cudaMalloc(&d_phi, n * sizeof(double)) != cudaSuccess) return NAN;
+    if (cudaMalloc(&d_R, 2 * n * sizeof(double)) != cudaSuccess) { cudaFree(d_phi); return NAN; }
+    std::vector<double> phi(n), R(2 * n);
+    double lo = 0.0, hi = 8.0 * p->fwhm_est;
+    double result = NAN;
+    bool found = false;
+    for (int expand = 0; expand < 4 && !found; ++expand) {
+        for (int round = 0; round < 3; ++round) {
+            for (int i = 0; i < n; ++i) phi[i] = lo + (hi - lo) * i / (n - 1);
+            if (cudaMemcpy(d_phi, phi.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+                launch_rmsf(*p, d_phi, n, d_R, nullptr, 0) != cudaSuccess ||
+                cudaMemcpy(R.data(), d_R, 2 * n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+                goto out;
+            int first = -1;
+            for (int i = 1; i < n; ++i)
+                if (std::hypot(R[2 * i], R[2 * i + 1]) <= 0.5) { first = i; break; }
+            if (first < 0) {
+                if (round > 0) goto out;
+                break;
+            }
+            lo = phi[first - 1];
+            hi = phi[first];
+            if (round == 2) {
+                double a = std::hypot(R[2 * (first - 1)], R[2 * (first - 1) + 1]);
+                double b = std::hypot(R[2 * first], R[2 * first + 1]);
+                double t = (a - 0.5) / (a - b);
+                result = 2.0 * (lo + t * (hi - lo));
+                found = true;
+            }
+        }
+        if (!found) { lo = 0.0; hi *= 8.0; }
+    }
+out:
+    cudaFree(d_phi);
+    cudaFree(d_R);
+    return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rms_status_string(rms_status s)
+{
+    switch (s) {
+    case RMS_OK: return "success";
+    case RMS_ERR_INVALID_ARG: return "invalid argument";
+    case RMS_ERR_OOM: return "out of memory";
+    case RMS_ERR_CUDA: return "CUDA error";
+    case RMS_ERR_UNSUPPORTED: return "unsupported device or precision";
+    case RMS_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, int32_t axis_kind,
+                           const double *weights, const double *phi, int32_t nphi, int32_t precision,
+                           int32_t device)
+{
+    if (!out) return RMS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!axis || !phi || nchan < 1 || nchan > 65536 || nphi < 1 || nphi > (1 << 20)) return RMS_ERR_INVALID_ARG;
+    if (axis_kind != RMS_AXIS_LAMBDA2 && axis_kind != RMS_AXIS_FREQ_HZ) return RMS_ERR_INVALID_ARG;
+    if (precision < RMS_FP32_SIMT_FLY || precision > RMS_FP16X3) return RMS_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return RMS_ERR_CUDA;
+    if (device < 0 || device >= ndev) return RMS_ERR_INVALID_ARG;
+
+    // plan constants (Sec. 2.2): lambda^2, K = 1/sum w, lambda_0^2 = weighted mean
+    std::vector<double> lam2(nchan), w(nchan);
+    double sw = 0.0, swl = 0.0, wmax = 0.0;
+    for (int i = 0; i < nchan; ++i) {
+        double a = axis[i];
+        if (!std::isfinite(a)) return RMS_ERR_INVALID_ARG;
+        if (axis_kind == RMS_AXIS_FREQ_HZ) {
+            if (!(a > 0.0)) return RMS_ERR_INVALID_ARG;
+            double lam = kCLight / a;
+            lam2[i] = lam * lam;
+        } else {
+            lam2[i] = a;
+        }
+        double wi = weights ? weights[i] : 1.0;
+        if (!std::isfinite(wi) || wi < 0.0) return RMS_ERR_INVALID_ARG;
+        w[i] = wi;
+        sw += wi;
+        swl += wi * lam2[i];
+        if (wi > wmax) wmax = wi;
+    }
+    if (!(sw > 0.0)) return RMS_ERR_INVALID_ARG;
+    for (int k = 0; k < nphi; ++k)
+        if (!std::isfinite(phi[k])) return RMS_ERR_INVALID_ARG;
+
+    DeviceGuard guard(device);
+    if (!guard.ok) return RMS_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return RMS_ERR_CUDA;
+    // the library's device code is built for sm_103a only
+    if (!(prop.major == 10 && prop.minor == 3)) return RMS_ERR_UNSUPPORTED;
+
+    rms_plan_s *p = new (std::nothrow) rms_plan_s();
+    if (!p) return RMS_ERR_OOM;
+    p->device = device;
+    p->nchan = nchan;
+    p->nphi = nphi;
+    p->precision = precision;
+    p->K = 1.0 / sw;
+    p->lambda0sq = swl / sw;
+    p->wmax = wmax;
+    p->lambda2 = lam2;
+    p->weights = w;
+    p->phi.assign(phi, phi + nphi);
+    p->num_sms = prop.multiProcessorCount;
+    std::vector<double> dl2, wact;
+    double lmin = INFINITY, lmax = -INFINITY;
+    for (int i = 0; i < nchan; ++i)
+        if (w[i] != 0.0) {
+            p->active.push_back(i);
+            dl2.push_back(lam2[i] - p->lambda0sq);
+            wact.push_back(w[i]);
+            lmin = std::fmin(lmin, lam2[i]);
+            lmax = std::fmax(lmax, lam2[i]);
+        }
+    p->nact = (int32_t)p->active.size();
+    p->fwhm_est = lmax > lmin ? 2.0 * std::sqrt(3.0) / (lmax - lmin) : INFINITY;
+    std::vector<float> phi32(nphi), l2x32(p->nact), w32(p->nact);
+    for (int k = 0; k < nphi; ++k) phi32[k] = (float)phi[k];
+    for (int a = 0; a < p->nact; ++a) {
+        l2x32[a] = (float)(2.0 * dl2[a]);
+        w32[a] = (float)wact[a];
+    }
+
+    cudaError_t e = cudaSuccess;
+#define RMS_TRY(x)                   \
+    do {                             \
+        e = (x);                     \
+        if (e != cudaSuccess) goto fail; \
+    } while (0)
+    RMS_TRY(cudaHostAlloc(reinterpret_cast<void **>(&p->h_err), sizeof(int), cudaHostAllocMapped));
+    *p->h_err = 0;
+    RMS_TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&p->d_err), p->h_err, 0));
+    RMS_TRY(dalloc(&p->d_active, p->nact));
+    RMS_TRY(dalloc(&p->d_dl2, p->nact));
+    RMS_TRY(dalloc(&p->d_wact, p->nact));
+    RMS_TRY(dalloc(&p->d_phi, nphi));
+    RMS_TRY(dalloc(&p->d_phi32, nphi));
+    RMS_TRY(dalloc(&p->d_l2x32, p->nact));
+    RMS_TRY(dalloc(&p->d_w32, p->nact));
+    RMS_TRY(dalloc(&p->d_R64, 2 * (size_t)nphi));
+    RMS_TRY(cudaMemcpy(p->d_active, p->active.data(), p->nact * sizeof(int32_t), cudaMemcpyHostToDevice));
+    RMS_TRY(cudaMemcpy(p->d_dl2, dl2.data(), p->nact * sizeof(double), cudaMemcpyHostToDevice));
+    RMS_TRY(cudaMemcpy(p->d_wact, wact.data(), p->nact * sizeof(double), cudaMemcpyHostToDevice));
+    RMS_TRY(cudaMemcpy(p->d_phi, phi, nphi * sizeof(double), cudaMemcpyHostToDevice));
+    RMS_TRY(cudaMemcpy(p->d_phi32, phi32.data(), nphi * sizeof(float), cudaMemcpyHostToDevice));
+    RMS_TRY(cudaMemcpy(p->d_l2x32, l2x32.data(), p->nact * sizeof(float), cudaMemcpyHostToDevice));
+    RMS_TRY(cudaMemcpy(p->d_w32, w32.data(), p->nact * sizeof(float), cudaMemcpyHostToDevice));
+
+    if (precision == RMS_FP32_SIMT_TABLE) {
+        RMS_TRY(dalloc(&p->d_table, (size_t)p->nact * nphi));
+        RMS_TRY(launch_phase_table(*p, 0));
+    } else if (is_tensor(precision)) {
+        const int N = 2 * nphi;
+        p->ntiles_n = (N + kMaxTileN - 1) / kMaxTileN;
+        int per = (N + p->ntiles_n - 1) / p->ntiles_n;
+        p->tile_n = (per + 15) / 16 * 16;
+        int last = N - (p->ntiles_n - 1) * p->tile_n;
+        p->tile_n_last = (last + 15) / 16 * 16;
+        p->npad = p->ntiles_n * p->tile_n;
+        p->kblocks = (p->nact + kChanPerKBlock - 1) / kChanPerKBlock;
+        p->kpad = p->kblocks * kKBlock;
+        RMS_TRY(dalloc(&p->d_bhi, (size_t)p->npad * p->kpad));
+        RMS_TRY(dalloc(&p->d_blo, (size_t)p->npad * p->kpad));
+        RMS_TRY(launch_phase_bsplit(*p, precision == RMS_FP16X3, 0));
+        if (!encode_b_map(&p->tmap_bhi, p->d_bhi, p->kpad, p->npad, p->tile_n) ||
+            !encode_b_map(&p->tmap_blo, p->d_blo, p->kpad, p->npad, p->tile_n)) {
+            free_plan(p);
+            return RMS_ERR_CUDA;
+        }
+    }
+    RMS_TRY(launch_rmsf(*p, p->d_phi, nphi, p->d_R64, nullptr, 0));
+    RMS_TRY(cudaDeviceSynchronize());
+    p->fwhm_meas = measure_fwhm(p);
+    RMS_TRY(cudaDeviceSynchronize());
+#undef RMS_TRY
+    *out = p;
+    return RMS_OK;
+fail:
+    cudaGetLastError();
+    free_plan(p);
+    return from_cuda(e);
+}
+
+rms_status rms_plan_destroy(rms_plan_t p)
+{
+    if (!p) return RMS_OK;
+    DeviceGuard guard(p->device);
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return RMS_OK;
+}
+
+rms_status rms_rmsf(rms_plan_t p, float *R_out, double *lambda0sq, double *K, double *fwhm_meas,
+                    double *fwhm_est)
+{
+    if (!p) return RMS_ERR_INVALID_ARG;
+    if (lambda0sq) *lambda0sq = p->lambda0sq;
+    if (K) *K = p->K;
+    if (fwhm_meas) *fwhm_meas = p->fwhm_meas;
+    if (fwhm_est) *fwhm_est = p->fwhm_est;
+    if (R_out) {
+        DeviceGuard guard(p->device);
+        cudaError_t e = launch_rmsf(*p, p->d_phi, p->nphi, nullptr, R_out, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return RMS_OK;
+}
+
+static rms_status synth_device(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    switch (p->precision) {
+    case RMS_FP32_SIMT_FLY:
+    case RMS_FP32_SIMT_TABLE:
+        e = launch_simt(*p, p->precision == RMS_FP32_SIMT_FLY, Q, U, nlos, layout, F, pidx, pabs, pphi, s);
+        break;
+    case RMS_BF16:
+    case RMS_BF16X3:
+        e = launch_umma(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, nullptr, s);
+        break;
+    case RMS_FP16X3: {
+        // per-LOS exponents: stream-ordered scratch of nlos bytes
+        int8_t *rexp = nullptr;
+        e = cudaMallocAsync(reinterpret_cast<void **>(&rexp), (size_t)nlos, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        e = launch_row_exponent(*p, Q, U, nlos, layout, rexp, s);
+        if (e == cudaSuccess) e = launch_umma(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, rexp, s);
+        cudaError_t e2 = cudaFreeAsync(rexp, s);
+        if (e == cudaSuccess) e = e2;
+        break;
+    }
+    default:
+        return RMS_ERR_INVALID_ARG;
+    }
+    return from_cuda(e);
+}
+
+static rms_status check_synth_args(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                                   float *F)
+{
+    if (!p || !Q || !U || nlos < 0) return RMS_ERR_INVALID_ARG;
+    if (layout != RMS_CHAN_MAJOR && layout != RMS_LOS_MAJOR) return RMS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(Q) & 3) || (reinterpret_cast<uintptr_t>(U) & 3)) return RMS_ERR_INVALID_ARG;
+    if (F && (reinterpret_cast<uintptr_t>(F) & 7)) return RMS_ERR_INVALID_ARG;
+    if (nlos > ((int64_t)1 << 40) / ((int64_t)p->nchan + p->nphi)) return RMS_ERR_INVALID_ARG;
+    return RMS_OK;
+}
+
+rms_status rms_synth(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout, float *F_out,
+                     int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream)
+{
+    rms_status st = check_synth_args(p, Q, U, nlos, layout, F_out);
+    if (st != RMS_OK) return st;
+    if (*p->h_err) return RMS_ERR_TIMEOUT;
+    if (nlos == 0 || (!F_out && !peak_idx && !peak_abs && !phi_peak)) return RMS_OK;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RMS_ERR_CUDA;
+    return synth_device(p, Q, U, nlos, layout, F_out, peak_idx, peak_abs, phi_peak,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout, float *F_out,
+                          int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream)
+{
+    rms_status st = check_synth_args(p, Q, U, nlos, layout, F_out);
+    if (st != RMS_OK) return st;
+    if (*p->h_err) return RMS_ERR_TIMEOUT;
+    if (nlos == 0 || (!F_out && !peak_idx && !peak_abs && !phi_peak)) return RMS_OK;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RMS_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t in_b = (size_t)nlos * p->nchan * sizeof(float);
+    const size_t f_b = F_out ? (size_t)nlos * p->nphi * 2 * sizeof(float) : 0;
+    const size_t pk_b = (size_t)nlos * sizeof(float);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t need = 2 * up(in_b) + up(f_b) + 3 * up(pk_b);
+    if (need > p->stage_bytes) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return from_cuda(e);
+        cudaFree(p->d_stage);
+        p->d_stage = nullptr;
+        p->stage_bytes = 0;
+        if (cudaMalloc(&p->d_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return RMS_ERR_OOM;
+        }
+        p->stage_bytes = need;
+    }
+    char *b = static_cast<char *>(p->d_stage);
+    float *dQ = reinterpret_cast<float *>(b);
+    float *dU = reinterpret_cast<float *>(b + up(in_b));
+    float *dF = F_out ? reinterpret_cast<float *>(b + 2 * up(in_b)) : nullptr;
+    char *pk = b + 2 * up(in_b) + up(f_b);
+    int32_t *dI = peak_idx ? reinterpret_cast<int32_t *>(pk) : nullptr;
+    float *dA = peak_abs ? reinterpret_cast<float *>(pk + up(pk_b)) : nullptr;
+    float *dP = phi_peak ? reinterpret_cast<float *>(pk + 2 * up(pk_b)) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dQ, Q, in_b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dU, U, in_b, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    st = synth_device(p, dQ, dU, nlos, layout, dF, dI, dA, dP, s);
+    if (st != RMS_OK) return st;
+    if (F_out) e = cudaMemcpyAsync(F_out, dF, f_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dI) e = cudaMemcpyAsync(peak_idx, dI, pk_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dA) e = cudaMemcpyAsync(peak_abs, dA, pk_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dP) e = cudaMemcpyAsync(phi_peak, dP, pk_b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return *p->h_err ? RMS_ERR_TIMEOUT : RMS_OK;
+}
+
+rms_status rms_plan_sync(rms_plan_t p, void *stream)
+{
+    if (!p) return RMS_ERR_INVALID_ARG;
+    DeviceGuard guard(p->device);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaGetLastError();
+    int err = *p->h_err;
+    *p->h_err = 0;
+    if (e != cudaSuccess) return RMS_ERR_CUDA;
+    return err ? RMS_ERR_TIMEOUT : RMS_OK;
+}
+
+rms_status rms_plan_set_timeout(rms_plan_t p, int64_t ns)
+{
+    if (!p || ns <= 0) return RMS_ERR_INVALID_ARG;
+    p->timeout_ns = ns;
+    return RMS_OK;
+}
+
+rms_status rms_plan_info(rms_plan_t p, int32_t what, int64_t *value)
+{
+    if (!p || !value) return RMS_ERR_INVALID_ARG;
+    switch (what) {
+    case RMS_INFO_NCHAN: *value = p->nchan; break;
+    case RMS_INFO_NCHAN_ACTIVE: *value = p->nact; break;
+    case RMS_INFO_NPHI: *value = p->nphi; break;
+    case RMS_INFO_PRECISION: *value = p->precision; break;
+    case RMS_INFO_KPAD: *value = p->kpad; break;
+    case RMS_INFO_NPAD: *value = p->npad; break;
+    case RMS_INFO_TILE_N: *value = p->tile_n; break;
+    case RMS_INFO_DEVICE: *value = p->device; break;
+    default: return RMS_ERR_INVALID_ARG;
+    }
+    return RMS_OK;
+}
+
+rms_status rms_plan_get(rms_plan_t p, int32_t what, void *dst, int64_t bytes)
+{
+    if (!p || !dst) return RMS_ERR_INVALID_ARG;
+    const void *src = nullptr;
+    size_t n = 0;
+    bool host = false;
+    switch (what) {
+    case RMS_GET_LAMBDA2: src = p->lambda2.data(); n = p->lambda2.size() * sizeof(double); host = true; break;
+    case RMS_GET_ACTIVE: src = p->active.data(); n = p->active.size() * sizeof(int32_t); host = true; break;
+    case RMS_GET_TABLE: src = p->d_table; n = (size_t)p->nact * p->nphi * sizeof(float2); break;
+    case RMS_GET_B_HI: src = p->d_bhi; n = (size_t)p->npad * p->kpad * sizeof(uint16_t); break;
+    case RMS_GET_B_LO: src = p->d_blo; n = (size_t)p->npad * p->kpad * sizeof(uint16_t); break;
+    case RMS_GET_RMSF64: src = p->d_R64; n = (size_t)p->nphi * 2 * sizeof(double); break;
+    default: return RMS_ERR_INVALID_ARG;
+    }
+    if (!src || (int64_t)n != bytes) return RMS_ERR_INVALID_ARG;
+    if (host) {
+        std::memcpy(dst, src, n);
+        return RMS_OK;
+    }
+    DeviceGuard guard(p->device);
+    return from_cuda(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/rms.h"
+
+// Device-side error codes written to the plan's error word.
+enum { RMS_DEVERR_NONE = 0, RMS_DEVERR_TIMEOUT = 1 };
+
+// Tensor-core tiling constants.
+constexpr int kTileM = 128;        // LOS rows per tile (UMMA M)
+constexpr int kChanPerKBlock = 16; // active channels per pipeline stage
+constexpr int kKBlock = 32;        // K values (Q and U interleaved) per stage = 64 bytes of bf16
+constexpr int kMaxTileN = 256;     // UMMA N limit for M = 128
+
+struct rms_plan_s {
+    int device = 0;
+    int32_t nchan = 0, nact = 0, nphi = 0, precision = 0;
+    double K = 0, lambda0sq = 0, wmax = 0, fwhm_meas = 0, fwhm_est = 0;
+    std::vector<double> lambda2, weights, phi;
+    std::vector<int32_t> active;
+
+    // device arrays
+    int32_t *d_active = nullptr;   // [nact] channel index of each active channel
+    double *d_dl2 = nullptr;       // [nact] lambda_j^2 - lambda_0^2 (FP64)
+    double *d_wact = nullptr;      // [nact] w_j
+    double *d_phi = nullptr;       // [nphi]
+    float *d_phi32 = nullptr;      // [nphi] phi rounded to FP32 (peak output)
+    float *d_l2x32 = nullptr;      // [nact] 2 (lambda_j^2 - lambda_0^2) in FP32 (FP32 on-the-fly path)
+    float *d_w32 = nullptr;        // [nact] w_j in FP32
+    float2 *d_table = nullptr;     // [nact][nphi] w_j (cos, sin) FP32 (table path)
+    uint16_t *d_bhi = nullptr;     // [npad][kpad] tensor-core phase matrix, high part
+    uint16_t *d_blo = nullptr;     // [npad][kpad] low part
+    double *d_R64 = nullptr;       // [nphi][2]
+    int32_t kpad = 0, npad = 0, tile_n = 0, ntiles_n = 0, tile_n_last = 0, kblocks = 0;
+    CUtensorMap tmap_bhi;   // CUtensorMap is 64-byte aligned by its own declaration
+    CUtensorMap tmap_blo;
+
+    // sticky device error word, mapped host memory (readable without a sync)
+    int *h_err = nullptr;
+    int *d_err = nullptr;
+    int64_t timeout_ns = 2000000000LL;
+    int num_sms = 0;
+
+    // rms_synth_host staging
+    size_t stage_bytes = 0;
+    void *d_stage = nullptr;
+
+    // FP16X3: per-LOS exponent scratch
+    size_t rexp_cap = 0;
+    int8_t *d_rexp = nullptr;
+};
+
+// phase.cu
+cudaError_t launch_phase_table(const rms_plan_s &p, cudaStream_t s);
+cudaError_t launch_phase_bsplit(const rms_plan_s &p, bool fp16, cudaStream_t s);
+cudaError_t launch_rmsf(const rms_plan_s &p, const double *d_phi, int32_t n, double *d_R64,
+                        float *d_R32, cudaStream_t s);
+
+// simt.cu
+cudaError_t launch_simt(const rms_plan_s &p, bool fly, const float *Q, const float *U, int64_t nlos,
+                        int layout, float *F, int32_t *pidx, float *pabs, float *pphi,
+                        cudaStream_t s);
+
+// umma.cu
+cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos,
+                        int layout, float *F, int32_t *pidx, float *pabs, float *pphi,
+                        const int8_t *rexp, cudaStream_t s);
+cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos,
+                                int layout, int8_t *rexp, cudaStream_t s);
+size_t umma_smem_bytes(int tile_n, int stages);
+int umma_stages(int tile_n);

@@ -1,0 +1,233 @@
+"""GPU parity: librms.so (through the C ABI) against the FP64 oracle.
+
+Inputs are seeded synthetic cubes from paper_1810_06250_gb300.inputs generated
+on the host; expected values come from oracle/ only.
+"""
+import numpy as np
+import pytest
+
+import gpu_helpers as gh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PATHS = ["fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3"]
+
+
+@pytest.fixture(scope="module")
+def rms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_06250_gb300 as rms
+    rms.build()
+    rms.load()
+    return rms
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    from paper_1810_06250_gb300 import inputs
+    return inputs
+
+
+def run(rms, plan, Q, U, layout, nlos, want_F=True, stream=None):
+    """Q, U: host float32 LOS-major [nlos][nchan]."""
+    dev = torch.device("cuda")
+    from paper_1810_06250_gb300.inputs import to_layout
+    q = torch.from_numpy(to_layout(Q, layout)).to(dev)
+    u = torch.from_numpy(to_layout(U, layout)).to(dev)
+    F = torch.full((nlos, plan.nphi, 2), float("nan"), device=dev) if want_F else None
+    pidx = torch.full((nlos,), -7, dtype=torch.int32, device=dev)
+    pabs = torch.zeros(nlos, device=dev)
+    pphi = torch.zeros(nlos, device=dev)
+    plan.synth(q, u, nlos, layout, F, pidx, pabs, pphi, stream)
+    plan.sync(stream)
+    torch.cuda.synchronize()
+    return (F.cpu().numpy() if want_F else None, pidx.cpu().numpy(), pabs.cpu().numpy(), pphi.cpu().numpy())
+
+
+def axes(inputs, cfg):
+    return inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
+
+
+# ------------------------------------------------------------------- plan
+@pytest.mark.parametrize("path", PATHS)
+def test_plan_constants(rms, inputs, oracle_mod, path):
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = axes(inputs, cfg)
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        op = oracle_mod.plan(freq, "freq", w)
+        l0, K, fm, fe = plan.rmsf()
+        assert abs(K - op.K) <= 1e-15 * op.K
+        assert abs(l0 - op.lambda0sq) <= 1e-14 * op.lambda0sq
+        np.testing.assert_allclose(plan.get(rms.RMS_GET_LAMBDA2), op.lambda2, rtol=1e-15)
+        np.testing.assert_array_equal(plan.get(rms.RMS_GET_ACTIVE), op.active)
+        R64 = plan.get(rms.RMS_GET_RMSF64)
+        Ro = oracle_mod.rmsf(op, phi)
+        np.testing.assert_allclose(R64[:, 0] + 1j * R64[:, 1], Ro, rtol=0, atol=1e-13)
+        R32 = torch.empty(2 * cfg.nphi, device="cuda")
+        plan.rmsf(R32)
+        r = R32.cpu().numpy().reshape(-1, 2)
+        np.testing.assert_allclose(r[:, 0] + 1j * r[:, 1], Ro, rtol=0, atol=2e-7)
+        assert abs(fe - oracle_mod.fwhm_estimate(op)) <= 1e-12 * fe
+        assert abs(fm - oracle_mod.fwhm_measured(op)) <= 1e-6 * fm
+
+
+def test_phase_table(rms, inputs, oracle_mod):
+    cfg = inputs.CONFIGS["mwa"]          # largest phases: |theta| up to ~7e4 rad
+    freq, w, phi = axes(inputs, cfg)
+    phi = phi[::7]
+    with rms.Plan(freq, phi, "fp32_table", weights=w) as plan:
+        op = oracle_mod.plan(freq, "freq", w)
+        tab = plan.get(rms.RMS_GET_TABLE)
+        act = op.active
+        th = 2.0 * phi[None, :] * (op.lambda2[act, None] - op.lambda0sq)
+        exp_c = w[act, None] * np.cos(th)
+        exp_s = w[act, None] * np.sin(th)
+        # FP32 rounding of an FP64 value accurate to ~1e-15
+        np.testing.assert_allclose(tab[..., 0], exp_c, rtol=0, atol=6.1e-8)
+        np.testing.assert_allclose(tab[..., 1], exp_s, rtol=0, atol=6.1e-8)
+
+
+def _bits_to_float(b, fp16):
+    if fp16:
+        return b.view(np.float16).astype(np.float64)
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("path", ["bf16x3", "fp16x3"])
+def test_phase_split_matrix(rms, inputs, oracle_mod, path):
+    cfg = inputs.CONFIGS["mwa"]
+    freq, w, phi = axes(inputs, cfg)
+    phi = phi[::13]
+    fp16 = path == "fp16x3"
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        op = oracle_mod.plan(freq, "freq", w)
+        hi = _bits_to_float(plan.get(rms.RMS_GET_B_HI), fp16)
+        lo = _bits_to_float(plan.get(rms.RMS_GET_B_LO), fp16)
+        B = hi + lo
+        act = op.active
+        nact, nphi = len(act), len(phi)
+        th = 2.0 * phi[None, :] * (op.lambda2[act, None] - op.lambda0sq)
+        wn = (w[act] / w.max())[:, None]
+        c, s = (wn * np.cos(th)).T, (wn * np.sin(th)).T          # [nphi][nact]
+        tol = 2.0 ** -16 if not fp16 else 2.0 ** -21
+        np.testing.assert_allclose(B[0:2 * nphi:2, 0:2 * nact:2], c, rtol=0, atol=tol)
+        np.testing.assert_allclose(B[0:2 * nphi:2, 1:2 * nact:2], s, rtol=0, atol=tol)
+        np.testing.assert_allclose(B[1:2 * nphi:2, 0:2 * nact:2], -s, rtol=0, atol=tol)
+        np.testing.assert_allclose(B[1:2 * nphi:2, 1:2 * nact:2], c, rtol=0, atol=tol)
+        assert not B[2 * nphi:, :].any() and not B[:, 2 * nact:].any()   # zero padding
+
+
+# ------------------------------------------------------------------- synthesis
+@pytest.mark.parametrize("layout", ["chan", "los"])
+@pytest.mark.parametrize("path", PATHS)
+def test_synth_tiny(rms, inputs, oracle_mod, path, layout):
+    cfg = inputs.CONFIGS["tiny"]
+    freq, w, phi = axes(inputs, cfg)
+    Q, U = inputs.make_cube(cfg)
+    op = oracle_mod.plan(freq, "freq", w)
+    Fo = oracle_mod.synth(Q, U, op, phi)
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        F, pidx, pabs, pphi = run(rms, plan, Q, U, layout, cfg.nlos)
+        ok, info = gh.gate(path, F[..., 0] + 1j * F[..., 1], Fo)
+        print(info)
+        assert ok, info
+        gh.check_peaks_self(F, pidx, pabs, pphi, phi)
+        gh.check_peaks_oracle(pidx, Fo, gh.TOL[path])
+        # peak-only mode gives the same peak map
+        _, pidx2, pabs2, pphi2 = run(rms, plan, Q, U, layout, cfg.nlos, want_F=False)
+        np.testing.assert_array_equal(pidx2, pidx)
+        np.testing.assert_array_equal(pabs2, pabs)
+        np.testing.assert_array_equal(pphi2, pphi)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_edges(rms, inputs, oracle_mod, path):
+    """Ragged LOS counts, odd channel counts with flags and NaN there, a NaN
+    in an active channel, an all-zero LOS, nphi = 1 and several N tiles."""
+    rng = np.random.default_rng(5)
+    nchan = 37
+    freq = np.linspace(120e6, 168e6, nchan)
+    w = rng.uniform(0.5, 1.5, nchan)
+    w[[0, 5, 6, 20, 36]] = 0.0
+    for nphi, nlos in ((1, 1), (130, 127), (130, 129), (101, 300), (300, 257)):
+        phi = np.linspace(-60, 60, nphi) if nphi > 1 else np.array([3.5])
+        Q = rng.normal(size=(nlos, nchan)).astype(np.float32)
+        U = rng.normal(size=(nlos, nchan)).astype(np.float32)
+        Q[:, w == 0] = np.nan
+        U[:, w == 0] = np.inf
+        if nlos > 3:
+            Q[2, 7] = np.nan       # active channel: this LOS becomes all-NaN
+            Q[3] = 0.0
+            U[3] = 0.0
+        op = oracle_mod.plan(freq, "freq", w)
+        Fo = oracle_mod.synth(Q, U, op, phi)
+        with rms.Plan(freq, phi, path, weights=w) as plan:
+            for layout in ("chan", "los"):
+                F, pidx, pabs, pphi = run(rms, plan, Q, U, layout, nlos)
+                good = np.all(np.isfinite(Fo), axis=1)
+                ok, info = gh.gate(path, F[good, :, 0] + 1j * F[good, :, 1], Fo[good])
+                assert ok, (nphi, nlos, layout, info)
+                assert np.all(np.isnan(F[~good]))
+                gh.check_peaks_self(F, pidx, pabs, pphi, phi)
+                if nlos > 3:
+                    assert pidx[2] == -1 and pidx[3] == 0
+                gh.check_peaks_oracle(pidx[good], Fo[good], gh.TOL[path])
+
+
+def test_zero_los_and_bad_args(rms, inputs):
+    cfg = inputs.CONFIGS["tiny"]
+    freq, w, phi = axes(inputs, cfg)
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        q = torch.zeros(cfg.nchan * 4, device="cuda")
+        F = torch.zeros(4, cfg.nphi, 2, device="cuda")
+        plan.synth(q, q, 0, "chan", F)           # nothing to do
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_synth(plan.handle, q, q, 4, 7, F)
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_synth(plan.handle, q, q, -1, "chan", F)
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_synth(plan.handle, q, q, 4, "chan", F.data_ptr() + 4)    # misaligned F
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_synth(plan.handle, 0, q, 4, "chan", F)                    # NULL Q
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+        plan.sync()
+    for bad in (dict(weights=np.zeros(cfg.nchan)), dict(weights=-w), dict(precision=9)):
+        kw = dict(weights=w, precision="bf16x3")
+        kw.update(bad)
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_plan_create(freq, kw["weights"], phi, kw["precision"])
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+    rms.rms_plan_destroy(None)
+
+
+# ------------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def lofar(inputs):
+    cfg = inputs.CONFIGS["lofar"]
+    Q, U = inputs.make_cube(cfg)
+    return cfg, Q, U
+
+
+@pytest.mark.parametrize("layout", ["chan", "los"])
+@pytest.mark.parametrize("path", PATHS)
+def test_lofar_full(rms, inputs, oracle_mod, lofar, path, layout):
+    """LOFAR-HBA-like cube at full size (512^2 LOS x 400 ch x 401 phi), the bench's
+    launch; 1024 sampled LOS against the oracle, peaks checked on every LOS."""
+    cfg, Q, U = lofar
+    freq, w, phi = axes(inputs, cfg)
+    rng = np.random.default_rng(77)
+    sample = np.unique(np.r_[0, cfg.nlos - 1, rng.choice(cfg.nlos, 1022, replace=False)])
+    op = oracle_mod.plan(freq, "freq", w)
+    Fo = oracle_mod.synth(Q[sample], U[sample], op, phi)
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        F, pidx, pabs, pphi = run(rms, plan, Q, U, layout, cfg.nlos)
+        ok, info = gh.gate(path, F[sample, :, 0] + 1j * F[sample, :, 1], Fo)
+        print(info)
+        assert ok, info
+        gh.check_peaks_self(F, pidx, pabs, pphi, phi)
+        gh.check_peaks_oracle(pidx[sample], Fo, gh.TOL[path])
