@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of RM synthesis on GB300: one JSON line on rank 0.
+
+A step is one rms_synth call over the LOFAR-HBA-like cube (512^2 LOS x 400
+channels, 10% flagged, x 401 phi; FP32 Q/U resident in HBM, complex64 F and
+the peak map written back to HBM) with the plan built once beforehand (the
+phase matrix and RMSF are per-dataset constants, Sec. 2.3).  The metric is
+G(LOS * active channel * phi)/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--path bf16x3] [--layout chan]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Multi-GPU (torchrun): every rank synthesises its own full cube (weak scaling,
+no collective on the data path); value = all ranks' units / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RM-synth G(LOS*chan*phi)/s at stated error vs FP64"
+UNIT = "G(LOS*chan*phi)/s"
+CONFIG_NAME = "lofar"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="bf16x3")
+    ap.add_argument("--layout", default="chan", choices=["chan", "los"])
+    ap.add_argument("--config", default=CONFIG_NAME)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-paths", action="store_true", help="skip timing the other precision paths")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+        return False
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        # samples under load only: drop the idle head/tail below 50% of max
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(cfg_name):
+    from paper_1810_06250_gb300 import inputs
+    cfg = inputs.CONFIGS[cfg_name]
+    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
+    Q, U = inputs.make_cube(cfg)
+    return inputs, cfg, freq, w, phi, Q, U
+
+
+def cpu_leg(cfg, freq, w, phi, Q, U, seconds, F_gpu_rows=None, rows=None):
+    """Time the FP64 oracle (as it stands) on a bounded LOS sample on all host cores.
+    Also returns the GPU-vs-FP64 error on the sampled rows when the GPU rows are given."""
+    import oracle
+    oracle.build()
+    op = oracle.plan(freq, "freq", w)
+    nact = int(np.count_nonzero(w))
+    # calibrate on 256 LOS, then size the sample for ~`seconds` of CPU work
+    t0 = time.perf_counter()
+    oracle.synth(Q[:256], U[:256], op, phi)
+    dt = time.perf_counter() - t0
+    n = int(min(cfg.nlos, max(256, 256 * seconds / max(dt, 1e-6))))
+    sel = rows if rows is not None else np.arange(n)
+    if rows is not None:
+        n = len(rows)
+    t0 = time.perf_counter()
+    Fo = oracle.synth(Q[sel], U[sel], op, phi)
+    dt = time.perf_counter() - t0
+    units = n * nact * len(phi)
+    out = {"value": units / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "%d of %d LOS (all %d active channels x %d phi), FP64 C oracle, OpenMP over LOS, %.1f s"
+                     % (n, cfg.nlos, nact, len(phi), dt)}
+    err = None
+    if F_gpu_rows is not None:
+        d = np.abs(F_gpu_rows - Fo)
+        per = d.max(axis=1) / np.abs(Fo).max(axis=1)
+        err = {"per_los_max": float(per.max()), "per_los_p999": float(np.quantile(per, 0.999)),
+               "cube": float(d.max() / np.abs(Fo).max()), "sample_los": int(n)}
+    return out, err
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    _, cfg, freq, w, phi, Q, U = make_inputs(args.config)
+    import oracle
+    oracle.build()
+    op = oracle.plan(freq, "freq", w)
+    nact = int(np.count_nonzero(w))
+    # each step = a bounded sample so that the whole run ends within a few minutes
+    budget = 150.0
+    t0 = time.perf_counter()
+    oracle.synth(Q[:128], U[:128], op, phi)
+    per_los = (time.perf_counter() - t0) / 128
+    n = int(max(16, min(cfg.nlos, budget / max(1, args.steps + args.warmup) / per_los)))
+    for i in range(args.warmup):
+        oracle.synth(Q[:n], U[:n], op, phi)
+    times = []
+    for i in range(args.steps):
+        s = (i * n) % max(1, cfg.nlos - n)
+        t0 = time.perf_counter()
+        oracle.synth(Q[s:s + n], U[s:s + n], op, phi)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    units = n * nact * len(phi) * len(times)
+    v = units / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(cfg, nact, args.layout), "sample_los_per_step": n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d LOS per step of %d" % (n, cfg.nlos)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(cfg, nact, layout):
+    return ("%s: %dx%d LOS x %d channels (%d active) %.0f-%.0f MHz x %d phi in [%g, %g] rad/m^2, FP32 Q/U %s-major, "
+            "complex64 F + peak map" % (cfg.name, int(round(cfg.nlos ** 0.5)), int(round(cfg.nlos ** 0.5)), cfg.nchan,
+                                        nact, cfg.nu0 / 1e6, cfg.nu1 / 1e6, cfg.nphi, cfg.phi_min, cfg.phi_max, layout))
+
+
+def time_steps(fn, stream, steps, warmup, torch, barrier=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        fn()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total = ev[0].elapsed_time(ev[-1])
+    if barrier:
+        barrier()
+    return total, per
+
+
+def run_ours(args):
+    import torch
+    import paper_1810_06250_gb300 as rms
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rms.build()
+    inputs, cfg, freq, w, phi, Q, U = make_inputs(args.config)
+    nact = int(np.count_nonzero(w))
+    L = cfg.nlos
+    from paper_1810_06250_gb300.inputs import to_layout
+    q = torch.from_numpy(to_layout(Q, args.layout)).to(dev)
+    u = torch.from_numpy(to_layout(U, args.layout)).to(dev)
+    F = torch.empty(L, cfg.nphi, 2, device=dev)
+    pidx = torch.empty(L, dtype=torch.int32, device=dev)
+    pabs = torch.empty(L, device=dev)
+    pphi = torch.empty(L, device=dev)
+    stream = torch.cuda.Stream(dev)
+    units = L * nact * cfg.nphi
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        barrier = dist.barrier
+
+    t_plan0 = time.perf_counter()
+    plan = rms.Plan(freq, phi, args.path, weights=w, device=local)
+    plan_ms = 1e3 * (time.perf_counter() - t_plan0)
+
+    def step():
+        plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
+
+    with torch.cuda.stream(stream):
+        with ClockSampler(local) as clk:
+            total_ms, per = time_steps(step, stream, args.steps, args.warmup, torch, barrier)
+    plan.sync(stream)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    value = world * units * args.steps / (tmax * 1e-3) / 1e9
+    avg_launch_ms = statistics.mean(per)
+
+    # roofline of the dominant kernel (the synthesis kernel: one launch per step)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    tensor_path = args.path in ("bf16", "bf16x3", "fp16x3")
+    useful_flops = 8.0 * units
+    terms = 1 if args.path == "bf16" else 3
+    hbm_bytes = L * (8.0 * (nact if args.layout == "chan" else cfg.nchan) + 8.0 * cfg.nphi + 12.0)
+    if tensor_path:
+        peak = peaks.get("bf16_tflops_sustained")
+        src = "measured sustained bf16 (MEASURED_PEAKS.json)" if peak else "fallback 1700 TFLOP/s sustained"
+        peak = peak or 1700.0
+        achieved = useful_flops / (avg_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": src,
+                "issued_tflops": achieved * terms, "issued_frac": achieved * terms / peak,
+                "hbm_gbs": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9,
+                "algorithmic": "8 flop per (LOS, active channel, phi); %d tensor products issued per flop" % terms}
+    else:
+        props = torch.cuda.get_device_properties(dev)
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = props.multi_processor_count * 128 * 2 * clk_mhz * 1e6 / 1e12
+        achieved = useful_flops / (avg_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock",
+                "hbm_gbs": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.path, "data": "synthetic",
+            "config": {"workload": workload_name(cfg, nact, args.layout), "nlos_per_gpu": L, "nchan": cfg.nchan,
+                       "nchan_active": nact, "nphi": cfg.nphi, "layout": args.layout,
+                       "l2": "inputs larger than L2 (0.84 GB in, 0.84 GB out per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "units_per_step_total_channels": L * cfg.nchan * cfg.nphi},
+            "roofline": roof, "gpu_launches": args.steps * (2 if args.path == "fp16x3" else 1),
+            "plan_ms": plan_ms, "clocks": clk.summary()}
+
+    if rank == 0 and world == 1 and not args.no_paths:
+        paths = {}
+        for p in ("fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3"):
+            if p == args.path:
+                paths[p] = {"value": value, "ms_per_step": tmax / args.steps}
+                continue
+            with rms.Plan(freq, phi, p, weights=w, device=local) as pl:
+                n = 5 if p.startswith("fp32") else 50
+
+                def st2(pl=pl):
+                    pl.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
+                with torch.cuda.stream(stream):
+                    tot, _ = time_steps(st2, stream, n, 2, torch)
+                pl.sync(stream)
+                paths[p] = {"value": units * n / (tot * 1e-3) / 1e9, "ms_per_step": tot / n}
+        line["paths"] = paths
+        # restore this path's output for the error check below
+        plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
+        plan.sync(stream)
+
+    if rank == 0 and world == 1 and not args.no_e2e:
+        Qh = torch.from_numpy(to_layout(Q, args.layout)).pin_memory()
+        Uh = torch.from_numpy(to_layout(U, args.layout)).pin_memory()
+        Fh = torch.empty(L, cfg.nphi, 2).pin_memory()
+        ih = torch.empty(L, dtype=torch.int32).pin_memory()
+        ah = torch.empty(L).pin_memory()
+        ph = torch.empty(L).pin_memory()
+
+        def e2e_step():
+            plan.synth_host(Qh, Uh, L, args.layout, Fh, ih, ah, ph, stream)
+        n_e2e = max(3, min(50, args.steps // 20))
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / n_e2e
+        line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
+                       "h2d_bytes_per_step": int(Qh.numel() * 4 + Uh.numel() * 4),
+                       "d2h_bytes_per_step": int(Fh.numel() * 4 + L * 12),
+                       "how": "rms_synth_host: pinned host Q/U -> device, synthesis, F and peak map -> pinned host, sync"}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rng = np.random.default_rng(12345)
+        sel = None
+        # size the sample from a calibration run, then check the GPU rows on it
+        import oracle
+        oracle.build()
+        op = oracle.plan(freq, "freq", w)
+        t0 = time.perf_counter()
+        oracle.synth(Q[:128], U[:128], op, phi)
+        per_los = (time.perf_counter() - t0) / 128
+        n = int(min(L, max(256, args.cpu_seconds / per_los)))
+        sel = np.sort(rng.choice(L, n, replace=False))
+        Fg = F[torch.from_numpy(sel).to(dev)].cpu().numpy()
+        cpu, err = cpu_leg(cfg, freq, w, phi, Q, U, args.cpu_seconds, Fg[..., 0] + 1j * Fg[..., 1], sel)
+        line["cpu_baseline"] = cpu
+        line["error_vs_fp64"] = err
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
