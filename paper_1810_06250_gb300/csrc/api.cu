@@ -59,6 +59,11 @@ void free_plan(rms_plan_s *p)
     cudaFree(p->d_bhi);
     cudaFree(p->d_blo);
     cudaFree(p->d_R64);
+    cudaFree(p->d_dl2_all);
+    cudaFree(p->d_w_all);
+    if (p->d_bhi_raw != p->d_bhi) cudaFree(p->d_bhi_raw);
+    if (p->d_blo_raw != p->d_blo) cudaFree(p->d_blo_raw);
+    cudaFree(p->d_kbmask);
     cudaFree(p->d_stage);
     cudaFree(p->d_rexp);
     if (p->h_err) cudaFreeHost(p->h_err);
@@ -81,16 +86,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 bool encode_b_map(CUtensorMap *map, void *base, int kpad, int npad, int tile_n)
 {
-    auto enc = get_encode();
-    if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)npad};
     cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
     cuuint32_t box[2] = {(cuuint32_t)kKBlock, (cuuint32_t)tile_n};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    return encode_tensor_map(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
 // FWHM of |R|'s main lobe: |R| is even in phi, so find the first phi > 0 where
@@ -139,6 +140,17 @@ out:
 }
 
 }  // namespace
+
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, void *base, const cuuint64_t *dims,
+                       const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr,
+                       CUtensorMapSwizzle swizzle)
+{
+    auto enc = get_encode();
+    if (!enc) return false;
+    CUresult r = enc(map, type, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 extern "C" {
 
@@ -269,11 +281,37 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
         p->npad = p->ntiles_n * p->tile_n;
         p->kblocks = (p->nact + kChanPerKBlock - 1) / kChanPerKBlock;
         p->kpad = p->kblocks * kKBlock;
+        const bool fp16 = precision == RMS_FP16X3;
         RMS_TRY(dalloc(&p->d_bhi, (size_t)p->npad * p->kpad));
         RMS_TRY(dalloc(&p->d_blo, (size_t)p->npad * p->kpad));
-        RMS_TRY(launch_phase_bsplit(*p, precision == RMS_FP16X3, 0));
+        RMS_TRY(launch_phase_bsplit(*p, p->d_dl2, p->d_wact, p->nact, p->kpad, p->d_bhi, p->d_blo, fp16, 0));
+        // LOS-major cubes contract over every channel (zero rows where flagged)
+        p->kblocks_raw = (nchan + kChanPerKBlock - 1) / kChanPerKBlock;
+        p->kpad_raw = p->kblocks_raw * kKBlock;
+        std::vector<uint16_t> kbmask(p->kblocks_raw, 0);
+        for (int i = 0; i < nchan; ++i)
+            if (w[i] != 0.0) kbmask[i / kChanPerKBlock] |= (uint16_t)(1u << (i % kChanPerKBlock));
+        RMS_TRY(dalloc(&p->d_kbmask, p->kblocks_raw));
+        RMS_TRY(cudaMemcpy(p->d_kbmask, kbmask.data(), p->kblocks_raw * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        if (p->nact == nchan) {
+            p->d_bhi_raw = p->d_bhi;
+            p->d_blo_raw = p->d_blo;
+        } else {
+            std::vector<double> dl2_all(nchan);
+            for (int i = 0; i < nchan; ++i) dl2_all[i] = lam2[i] - p->lambda0sq;
+            RMS_TRY(dalloc(&p->d_dl2_all, nchan));
+            RMS_TRY(dalloc(&p->d_w_all, nchan));
+            RMS_TRY(cudaMemcpy(p->d_dl2_all, dl2_all.data(), nchan * sizeof(double), cudaMemcpyHostToDevice));
+            RMS_TRY(cudaMemcpy(p->d_w_all, w.data(), nchan * sizeof(double), cudaMemcpyHostToDevice));
+            RMS_TRY(dalloc(&p->d_bhi_raw, (size_t)p->npad * p->kpad_raw));
+            RMS_TRY(dalloc(&p->d_blo_raw, (size_t)p->npad * p->kpad_raw));
+            RMS_TRY(launch_phase_bsplit(*p, p->d_dl2_all, p->d_w_all, nchan, p->kpad_raw, p->d_bhi_raw,
+                                        p->d_blo_raw, fp16, 0));
+        }
         if (!encode_b_map(&p->tmap_bhi, p->d_bhi, p->kpad, p->npad, p->tile_n) ||
-            !encode_b_map(&p->tmap_blo, p->d_blo, p->kpad, p->npad, p->tile_n)) {
+            !encode_b_map(&p->tmap_blo, p->d_blo, p->kpad, p->npad, p->tile_n) ||
+            !encode_b_map(&p->tmap_bhi_raw, p->d_bhi_raw, p->kpad_raw, p->npad, p->tile_n) ||
+            !encode_b_map(&p->tmap_blo_raw, p->d_blo_raw, p->kpad_raw, p->npad, p->tile_n)) {
             free_plan(p);
             return RMS_ERR_CUDA;
         }

@@ -136,20 +136,23 @@ cudaError_t launch_phase_table(const rms_plan_s &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_phase_bsplit(const rms_plan_s &p, bool fp16, cudaStream_t s)
+// B over the channel list (dl2, w)[0..nk): the active channels for channel-major
+// cubes, or every channel (w = 0 where flagged, giving zero rows) for LOS-major.
+cudaError_t launch_phase_bsplit(const rms_plan_s &p, const double *dl2, const double *w, int32_t nk,
+                                int32_t kpad, uint16_t *bhi, uint16_t *blo, bool fp16, cudaStream_t s)
 {
-    size_t bytes = (size_t)p.npad * p.kpad * sizeof(uint16_t);
-    cudaError_t e = cudaMemsetAsync(p.d_bhi, 0, bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.d_blo, 0, bytes, s);
+    size_t bytes = (size_t)p.npad * kpad * sizeof(uint16_t);
+    cudaError_t e = cudaMemsetAsync(bhi, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(blo, 0, bytes, s);
     if (e != cudaSuccess) return e;
-    int64_t total = (int64_t)p.nact * p.nphi;
+    int64_t total = (int64_t)nk * p.nphi;
     double inv = 1.0 / p.wmax;
     if (fp16)
-        phase_bsplit_kernel<__half><<<grid_for(total, 256), 256, 0, s>>>(
-            p.d_dl2, p.d_wact, p.d_phi, p.nact, p.nphi, inv, p.kpad, p.d_bhi, p.d_blo);
+        phase_bsplit_kernel<__half><<<grid_for(total, 256), 256, 0, s>>>(dl2, w, p.d_phi, nk, p.nphi, inv, kpad,
+                                                                          bhi, blo);
     else
-        phase_bsplit_kernel<__nv_bfloat16><<<grid_for(total, 256), 256, 0, s>>>(
-            p.d_dl2, p.d_wact, p.d_phi, p.nact, p.nphi, inv, p.kpad, p.d_bhi, p.d_blo);
+        phase_bsplit_kernel<__nv_bfloat16><<<grid_for(total, 256), 256, 0, s>>>(dl2, w, p.d_phi, nk, p.nphi, inv,
+                                                                                 kpad, bhi, blo);
     return cudaGetLastError();
 }
 

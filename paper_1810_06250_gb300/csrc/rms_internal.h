@@ -16,7 +16,9 @@ enum { RMS_DEVERR_NONE = 0, RMS_DEVERR_TIMEOUT = 1 };
 constexpr int kTileM = 128;        // LOS rows per tile (UMMA M)
 constexpr int kChanPerKBlock = 16; // active channels per pipeline stage
 constexpr int kKBlock = 32;        // K values (Q and U interleaved) per stage = 64 bytes of bf16
-constexpr int kMaxTileN = 256;     // UMMA N limit for M = 128
+constexpr int kMaxTileN = 208;     // phase-matrix rows per tile: each of the two epilogue warps
+                                   // sharing a row keeps tile_n / 2 FP32 sums in registers
+constexpr int kGroupKBlocks = 6;   // K blocks accumulated in TMEM before the FP32 register fold
 
 struct rms_plan_s {
     int device = 0;
@@ -40,6 +42,15 @@ struct rms_plan_s {
     int32_t kpad = 0, npad = 0, tile_n = 0, ntiles_n = 0, tile_n_last = 0, kblocks = 0;
     CUtensorMap tmap_bhi;   // CUtensorMap is 64-byte aligned by its own declaration
     CUtensorMap tmap_blo;
+    // LOS-major cubes contract over all channels (flagged ones zeroed in the
+    // converter, zero rows in B), so their data tiles are contiguous boxes
+    double *d_dl2_all = nullptr;   // [nchan]
+    double *d_w_all = nullptr;     // [nchan]
+    uint16_t *d_bhi_raw = nullptr, *d_blo_raw = nullptr;   // [npad][kpad_raw]; alias d_bhi/d_blo if no flags
+    uint16_t *d_kbmask = nullptr;  // [kblocks_raw] bit i: channel 16 kb + i is active
+    int32_t kpad_raw = 0, kblocks_raw = 0;
+    CUtensorMap tmap_bhi_raw;
+    CUtensorMap tmap_blo_raw;
 
     // sticky device error word, mapped host memory (readable without a sync)
     int *h_err = nullptr;
@@ -58,7 +69,8 @@ struct rms_plan_s {
 
 // phase.cu
 cudaError_t launch_phase_table(const rms_plan_s &p, cudaStream_t s);
-cudaError_t launch_phase_bsplit(const rms_plan_s &p, bool fp16, cudaStream_t s);
+cudaError_t launch_phase_bsplit(const rms_plan_s &p, const double *dl2, const double *w, int32_t nk,
+                                int32_t kpad, uint16_t *bhi, uint16_t *blo, bool fp16, cudaStream_t s);
 cudaError_t launch_rmsf(const rms_plan_s &p, const double *d_phi, int32_t n, double *d_R64,
                         float *d_R32, cudaStream_t s);
 
@@ -73,5 +85,8 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
                         const int8_t *rexp, cudaStream_t s);
 cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos,
                                 int layout, int8_t *rexp, cudaStream_t s);
-size_t umma_smem_bytes(int tile_n, int stages);
-int umma_stages(int tile_n);
+
+// api.cu: cuTensorMapEncodeTiled through the runtime's driver entry point
+bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, void *base, const cuuint64_t *dims,
+                       const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr,
+                       CUtensorMapSwizzle swizzle);
