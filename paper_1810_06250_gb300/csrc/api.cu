@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "rms_internal.h"
@@ -66,6 +67,8 @@ void free_plan(rms_plan_s *p)
     cudaFree(p->d_kbmask);
     cudaFree(p->d_stage);
     cudaFree(p->d_rexp);
+    cudaFree(p->d_scratch);
+    if (p->last) cudaEventDestroy(p->last);
     if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
 }
@@ -308,6 +311,8 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
             RMS_TRY(launch_phase_bsplit(*p, p->d_dl2_all, p->d_w_all, nchan, p->kpad_raw, p->d_bhi_raw,
                                         p->d_blo_raw, fp16, 0));
         }
+        p->scratch_bytes = (size_t)p->num_sms * (size_t)std::max(p->kblocks, p->kblocks_raw) * kTileM * 128;
+        RMS_TRY(cudaMalloc(&p->d_scratch, p->scratch_bytes));
         if (!encode_b_map(&p->tmap_bhi, p->d_bhi, p->kpad, p->npad, p->tile_n) ||
             !encode_b_map(&p->tmap_blo, p->d_blo, p->kpad, p->npad, p->tile_n) ||
             !encode_b_map(&p->tmap_bhi_raw, p->d_bhi_raw, p->kpad_raw, p->npad, p->tile_n) ||
@@ -316,6 +321,7 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
             return RMS_ERR_CUDA;
         }
     }
+    RMS_TRY(cudaEventCreateWithFlags(&p->last, cudaEventDisableTiming));
     RMS_TRY(launch_rmsf(*p, p->d_phi, nphi, p->d_R64, nullptr, 0));
     RMS_TRY(cudaDeviceSynchronize());
     p->fwhm_meas = measure_fwhm(p);
@@ -355,7 +361,22 @@ rms_status rms_rmsf(rms_plan_t p, float *R_out, double *lambda0sq, double *K, do
     return RMS_OK;
 }
 
+static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s);
+
 static rms_status synth_device(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s)
+{
+    // the plan's scratch is shared by its calls: order them on the device
+    cudaError_t e = cudaStreamWaitEvent(s, p->last, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    rms_status st = synth_launch(p, Q, U, nlos, layout, F, pidx, pabs, pphi, s);
+    e = cudaEventRecord(p->last, s);
+    if (st == RMS_OK && e != cudaSuccess) st = from_cuda(e);
+    return st;
+}
+
+static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
                                float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;

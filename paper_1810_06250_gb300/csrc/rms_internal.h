@@ -62,6 +62,12 @@ struct rms_plan_s {
     size_t stage_bytes = 0;
     void *d_stage = nullptr;
 
+    // tensor paths: per-CTA split-A scratch, [num_sms][max kblocks][128][128 B]
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // calls on one plan are ordered on the device through this event (they share the scratch)
+    cudaEvent_t last = nullptr;
+
     // FP16X3: per-LOS exponent scratch
     size_t rexp_cap = 0;
     int8_t *d_rexp = nullptr;

@@ -27,6 +27,9 @@
 //                K-major layout), flagged / padded channels zeroed        -> fullA, emptyD
 //   warps 8..15  epilogue: warp w owns TMEM lane quarter w % 4 and column half
 //                (w - 8) / 4; folds partials, scales, peak, stores F      -> tempty
+// The split A tile of an M tile is converted once, on its first N tile, and kept
+// in a per-CTA scratch region (L2-resident for LOFAR-sized cubes) from which the
+// converters reload it for the remaining N tiles.
 // Without TMA-compatible strides the converters load FP32 directly instead.
 // Every mbarrier wait is bounded by a wall-clock limit; a wait that runs out
 // raises a CTA-wide abort flag and the device error word, every role leaves
@@ -52,10 +55,10 @@ constexpr int kStageD = kTileM * kChanPerKBlock * 4; // 8 KB of FP32 per Q or U
 constexpr int kTmemCols = 512;
 constexpr int kAccStride = 256;                     // TMEM columns per partial
 constexpr int kHalf = kMaxTileN / 2;                // 104 columns per epilogue thread
-constexpr int kEpiLd = 33;
+constexpr int kEpiLd = 17;                          // 16-column staging chunks
 constexpr int kEpiStageBytes = kNumEpiWarps * 32 * kEpiLd * 4;
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kRegsLow = 104, kRegsHigh = 152;      // setmaxnreg split: 256*104 + 256*152 = 512*128
+constexpr int kRegsLow = 96, kRegsHigh = 160;       // setmaxnreg split: 256*96 + 256*160 = 512*128
 
 enum { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_FP16X3 = 2 };
 
@@ -76,7 +79,9 @@ struct UmmaParams {
     const int8_t *rexp;
     int *err;
     int64_t timeout_ns;
-    int32_t sd, sm;             // stages of the FP32 data ring and of the A/B ring
+    int32_t sd, sa, sb;         // stages of the FP32 data, A and B rings
+    int32_t reuse;              // 1: convert on the first N tile only, reload from scratch after
+    uint4 *scratch;             // [grid][kblocks][16 KB]: split A stages of the current M tile (smem image)
 };
 
 // ----------------------------------------------------------------------------
@@ -164,6 +169,21 @@ __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_n(uint32_t bar, uint32_t n)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(n) : "memory");
+}
+// Orders this thread's generic-proxy accesses (shared and global) before later
+// async-proxy accesses (TMA, tensor core).
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -223,58 +243,62 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // ----------------------------------------------------------------------------
 // Converter helpers
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void split_bf16(float x, uint32_t &hi, uint32_t &lo)
+// Split a (Q, U) pair into packed hi and lo 16-bit pairs (Q in the low half):
+// hi = rn(x), lo = rn(x - hi), two values per conversion instruction.
+__device__ __forceinline__ void split_pair_bf16(float q, float u, uint32_t &hi, uint32_t &lo)
 {
-    __nv_bfloat16 h = __float2bfloat16_rn(x);
-    __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    hi = (uint32_t)__bfloat16_as_ushort(h);
-    lo = (uint32_t)__bfloat16_as_ushort(l);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(q, u);
+    const uint32_t hb = *reinterpret_cast<const uint32_t *>(&h);
+    const float qh = __uint_as_float(hb << 16), uh = __uint_as_float(hb & 0xffff0000u);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(q - qh, u - uh);
+    hi = hb;
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
-__device__ __forceinline__ void split_fp16(float x, uint32_t &hi, uint32_t &lo)
+__device__ __forceinline__ void split_pair_fp16(float q, float u, uint32_t &hi, uint32_t &lo)
 {
-    __half h = __float2half_rn(x);
-    __half l = __float2half_rn(x - __half2float(h));
-    hi = (uint32_t)__half_as_ushort(h);
-    lo = (uint32_t)__half_as_ushort(l);
+    const __half2 h = __floats2half2_rn(q, u);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(q - hf.x, u - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // Convert one row's 16 channels (K values Q0 U0 Q1 U1 ...) into the four 16-byte
 // chunks of the hi tile (and of the lo tile).  Row m, chunk c of a 64-byte-
-// swizzled K-major tile lives at m * 64 + ((c ^ ((m >> 1) & 3)) << 4).
+// swizzled K-major tile lives at m * 64 + ((c ^ ((m >> 1) & 3)) << 4).  When
+// scr is set, the same bytes also go to the scratch image of this stage
+// (hi part at scr, lo part at scr + 8 KB).
 __device__ __forceinline__ void convert_row(const float (&q)[16], const float (&u)[16], float scale, int mode,
-                                            uint8_t *a_hi, uint8_t *a_lo, int m)
+                                            uint8_t *a_hi, uint8_t *a_lo, int m, int sw, uint8_t *scr)
 {
-    const int sw = (m >> 1) & 3;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = 4 * c + j;
-            uint32_t qh, ql, uh, ul;
-            if (mode == MODE_FP16X3) {
-                split_fp16(q[i] * scale, qh, ql);
-                split_fp16(u[i] * scale, uh, ul);
-            } else {
-                split_bf16(q[i], qh, ql);
-                split_bf16(u[i], uh, ul);
-            }
-            hi[j] = qh | (uh << 16);
-            lo[j] = ql | (ul << 16);
+            if (mode == MODE_FP16X3) split_pair_fp16(q[i] * scale, u[i] * scale, hi[j], lo[j]);
+            else split_pair_bf16(q[i], u[i], hi[j], lo[j]);
         }
         const uint32_t off = (uint32_t)m * kRowBytes + ((uint32_t)(c ^ sw) << 4);
-        *reinterpret_cast<uint4 *>(a_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        if (mode != MODE_BF16) *reinterpret_cast<uint4 *>(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        const uint4 vh = make_uint4(hi[0], hi[1], hi[2], hi[3]), vl = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<uint4 *>(a_hi + off) = vh;
+        if (mode != MODE_BF16) *reinterpret_cast<uint4 *>(a_lo + off) = vl;
+        if (scr) {
+            *reinterpret_cast<uint4 *>(scr + off) = vh;
+            if (mode != MODE_BF16) *reinterpret_cast<uint4 *>(scr + kStageA + off) = vl;
+        }
     }
 }
 
 struct Smem {
-    uint8_t *dring, *mring;
-    uint32_t mstage;
+    uint8_t *dring, *aring, *bring;
+    uint32_t bstage;
     float *epi;
     float *pk_m;
     int *pk_i;
-    uint64_t *fullD, *emptyD, *fullB, *fullA, *emptyM, *tfull, *tempty, *pkfull, *pkempty, *mma_done;
+    uint64_t *fullD, *emptyD, *fullA, *emptyA, *fullB, *emptyB, *tfull, *tempty, *pkfull, *pkempty, *scr_ready,
+        *mma_done;
     uint32_t *tmem_slot;
     volatile int *abort_flag;
 };
@@ -282,26 +306,48 @@ struct Smem {
 __device__ __forceinline__ Smem carve(uint8_t *base, const UmmaParams &P)
 {
     Smem s;
+    s.bstage = 2 * (uint32_t)P.tile_n * kRowBytes;
     s.dring = base;
-    s.mstage = 2 * kStageA + 2 * (uint32_t)P.tile_n * kRowBytes;
-    s.mring = s.dring + (size_t)P.sd * 2 * kStageD;
-    s.epi = reinterpret_cast<float *>(s.mring + (size_t)P.sm * s.mstage);
+    s.aring = s.dring + (size_t)P.sd * 2 * kStageD;
+    s.bring = s.aring + (size_t)P.sa * 2 * kStageA;
+    s.epi = reinterpret_cast<float *>(s.bring + (size_t)P.sb * s.bstage);
     s.pk_m = s.epi + kEpiStageBytes / 4;
     s.pk_i = reinterpret_cast<int *>(s.pk_m + 2 * 4 * 32);
     uint64_t *b = reinterpret_cast<uint64_t *>(s.pk_i + 2 * 4 * 32);
     s.fullD = b;
-    s.emptyD = b + P.sd;
-    s.fullB = b + 2 * P.sd;
-    s.fullA = s.fullB + P.sm;
-    s.emptyM = s.fullA + P.sm;
-    s.tfull = s.emptyM + P.sm;
+    s.emptyD = s.fullD + P.sd;
+    s.fullA = s.emptyD + P.sd;
+    s.emptyA = s.fullA + P.sa;
+    s.fullB = s.emptyA + P.sa;
+    s.emptyB = s.fullB + P.sb;
+    s.tfull = s.emptyB + P.sb;
     s.tempty = s.tfull + 2;
     s.pkfull = s.tempty + 2;      // [2 parities][4 quarters]
     s.pkempty = s.pkfull + 8;
-    s.mma_done = s.pkempty + 8;
+    s.scr_ready = s.pkempty + 8;  // [2 parities]
+    s.mma_done = s.scr_ready + 2;
     s.tmem_slot = reinterpret_cast<uint32_t *>(s.mma_done + 1);
     s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
     return s;
+}
+
+// Ring position: slot index and phase parity.
+struct Ring {
+    int s = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int n)
+    {
+        if (++s == n) { s = 0; ph ^= 1; }
+    }
+};
+
+// Wait (bounded) for every copy this thread issued into a ring to land.
+__device__ __forceinline__ void drain(const uint64_t *full, int n, uint32_t pending, uint32_t pend_par,
+                                      volatile int *abort_flag, int *err, int64_t limit)
+{
+    for (int i = 0; i < n; ++i)
+        if (pending & (1u << i))
+            wait_bounded(smem_u32(&full[i]), (pend_par >> i) & 1, abort_flag, err, limit, false);
 }
 
 // ----------------------------------------------------------------------------
@@ -319,20 +365,25 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
     const int64_t nmt = (P.nlos + kTileM - 1) / kTileM;
     const bool split = P.mode != MODE_BF16;
     const int ngroups = (P.kblocks + P.group - 1) / P.group;
+    const uint32_t a_bytes = split ? 2 * kStageA : kStageA;   // one A stage (hi [+ lo])
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.sd; ++s) {
             mbar_init(smem_u32(&S.fullD[s]), 1);
             mbar_init(smem_u32(&S.emptyD[s]), kNumConvWarps);
         }
-        for (int s = 0; s < P.sm; ++s) {
+        for (int s = 0; s < P.sa; ++s) {
+            mbar_init(smem_u32(&S.fullA[s]), kNumConvWarps);   // converters, or producer: 1 + tx + 3
+            mbar_init(smem_u32(&S.emptyA[s]), 1);
+        }
+        for (int s = 0; s < P.sb; ++s) {
             mbar_init(smem_u32(&S.fullB[s]), 1);
-            mbar_init(smem_u32(&S.fullA[s]), kNumConvWarps);
-            mbar_init(smem_u32(&S.emptyM[s]), 1);
+            mbar_init(smem_u32(&S.emptyB[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.tfull[b]), 1);
             mbar_init(smem_u32(&S.tempty[b]), kNumEpiWarps);
+            mbar_init(smem_u32(&S.scr_ready[b]), kNumConvWarps);
         }
         for (int i = 0; i < 8; ++i) {
             mbar_init(smem_u32(&S.pkfull[i]), 1);
@@ -356,159 +407,192 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
     if (warp < kEpiWarp0) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
         if (warp == 0) {
-        // ------------------------------------------------------------ data producer
-        if (lane == 0 && P.use_tma) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmQ)) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmU)) : "memory");
-            int s = 0;
-            uint32_t ph = 0, pending = 0, pend_par = 0;
-            bool ok = true;
-            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
-                for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
-                    for (int kb = 0; kb < P.kblocks; ++kb) {
-                        if (!wait_bounded(smem_u32(&S.emptyD[s]), ph ^ 1, S.abort_flag, P.err, P.timeout_ns)) {
+            // -------------------------------------------------------- data / A producer
+            // first N tile: FP32 Q/U tiles into the data ring (converters split them);
+            // later N tiles: the split A tile written to scratch on the first N tile,
+            // one bulk copy per stage straight into the A ring.
+            if (lane == 0) {
+                if (P.use_tma) {
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmQ)) : "memory");
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmU)) : "memory");
+                }
+                Ring rd, ra;
+                uint32_t pendD = 0, parD = 0, pendA = 0, parA = 0;
+                bool ok = true;
+                int mt_count = 0;
+                for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count)
+                    for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
+                        if (P.reuse && nt == 1 &&
+                            !wait_bounded(smem_u32(&S.scr_ready[mt_count & 1]), (mt_count >> 1) & 1, S.abort_flag,
+                                          P.err, P.timeout_ns)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t dq = smem_u32(S.dring + (size_t)s * 2 * kStageD), du = dq + kStageD;
-                        const uint32_t bar = smem_u32(&S.fullD[s]);
-                        mbar_arrive_expect_tx(bar, 2 * kStageD);
-                        const int32_t m0 = (int32_t)(mt * kTileM);
-                        if (P.layout == RMS_CHAN_MAJOR) {
-#pragma unroll
-                            for (int g = 0; g < 4; ++g) {
-                                int32_t y[4];
-#pragma unroll
-                                for (int r = 0; r < 4; ++r) {
-                                    const int a = kb * kChanPerKBlock + 4 * g + r;
-                                    y[r] = __ldg(P.active + (a < P.nk ? a : P.nk - 1));
+                        for (int kb = 0; kb < P.kblocks; ++kb) {
+                            if (nt == 0 || !P.reuse) {
+                                ra.next(P.sa);      // the converters fill this A slot
+                                if (!P.use_tma) continue;
+                                if (!wait_bounded(smem_u32(&S.emptyD[rd.s]), rd.ph ^ 1, S.abort_flag, P.err,
+                                                  P.timeout_ns)) {
+                                    ok = false;
+                                    break;
                                 }
-                                tma_gather4(dq + g * 4 * kTileM * 4, &tmQ, m0, y[0], y[1], y[2], y[3], bar);
-                                tma_gather4(du + g * 4 * kTileM * 4, &tmU, m0, y[0], y[1], y[2], y[3], bar);
+                                const uint32_t dq = smem_u32(S.dring + (size_t)rd.s * 2 * kStageD), du = dq + kStageD;
+                                const uint32_t bar = smem_u32(&S.fullD[rd.s]);
+                                mbar_arrive_expect_tx(bar, 2 * kStageD);
+                                const int32_t m0 = (int32_t)(mt * kTileM);
+                                if (P.layout == RMS_CHAN_MAJOR) {
+#pragma unroll
+                                    for (int g = 0; g < 4; ++g) {
+                                        int32_t y[4];
+#pragma unroll
+                                        for (int r = 0; r < 4; ++r) {
+                                            const int a = kb * kChanPerKBlock + 4 * g + r;
+                                            y[r] = __ldg(P.active + (a < P.nk ? a : P.nk - 1));
+                                        }
+                                        tma_gather4(dq + g * 4 * kTileM * 4, &tmQ, m0, y[0], y[1], y[2], y[3], bar);
+                                        tma_gather4(du + g * 4 * kTileM * 4, &tmU, m0, y[0], y[1], y[2], y[3], bar);
+                                    }
+                                } else {
+                                    tma_load_2d(dq, &tmQ, kb * kChanPerKBlock, m0, bar);
+                                    tma_load_2d(du, &tmU, kb * kChanPerKBlock, m0, bar);
+                                }
+                                pendD |= 1u << rd.s;
+                                parD = (parD & ~(1u << rd.s)) | (rd.ph << rd.s);
+                                rd.next(P.sd);
+                            } else {
+                                if (!wait_bounded(smem_u32(&S.emptyA[ra.s]), ra.ph ^ 1, S.abort_flag, P.err,
+                                                  P.timeout_ns)) {
+                                    ok = false;
+                                    break;
+                                }
+                                const uint32_t bar = smem_u32(&S.fullA[ra.s]);
+                                mbar_arrive_expect_tx(bar, a_bytes);
+                                bulk_load(smem_u32(S.aring + (size_t)ra.s * 2 * kStageA),
+                                          P.scratch + ((size_t)blockIdx.x * P.kblocks + kb) * (2 * kStageA / 16),
+                                          a_bytes, bar);
+                                mbar_arrive_n(bar, kNumConvWarps - 1);
+                                pendA |= 1u << ra.s;
+                                parA = (parA & ~(1u << ra.s)) | (ra.ph << ra.s);
+                                ra.next(P.sa);
                             }
-                        } else {
-                            tma_load_2d(dq, &tmQ, kb * kChanPerKBlock, m0, bar);
-                            tma_load_2d(du, &tmU, kb * kChanPerKBlock, m0, bar);
                         }
-                        pending |= 1u << s;
-                        pend_par = (pend_par & ~(1u << s)) | (ph << s);
-                        if (++s == P.sd) { s = 0; ph ^= 1; }
                     }
-            if (!ok)
-                for (int i = 0; i < P.sd; ++i)
-                    if (pending & (1u << i))
-                        wait_bounded(smem_u32(&S.fullD[i]), (pend_par >> i) & 1, S.abort_flag, P.err, P.timeout_ns,
-                                     false);
-        }
-    } else if (warp == 2) {
-        // ------------------------------------------------------------ phase producer
-        if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_lo)) : "memory");
-            const uint32_t b_bytes = (uint32_t)P.tile_n * kRowBytes;
-            const uint32_t tx = split ? 2 * b_bytes : b_bytes;
-            int s = 0;
-            uint32_t ph = 0, pending = 0, pend_par = 0;
-            bool ok = true;
-            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
-                for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
-                    for (int kb = 0; kb < P.kblocks; ++kb) {
-                        if (!wait_bounded(smem_u32(&S.emptyM[s]), ph ^ 1, S.abort_flag, P.err, P.timeout_ns)) {
-                            ok = false;
-                            break;
+                if (!ok) {
+                    drain(S.fullD, P.sd, pendD, parD, S.abort_flag, P.err, P.timeout_ns);
+                    drain(S.fullA, P.sa, pendA, parA, S.abort_flag, P.err, P.timeout_ns);
+                }
+            }
+        } else if (warp == 2) {
+            // -------------------------------------------------------- phase producer
+            if (lane == 0) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_lo)) : "memory");
+                const uint32_t b_bytes = (uint32_t)P.tile_n * kRowBytes;
+                const uint32_t tx = split ? 2 * b_bytes : b_bytes;
+                Ring rb;
+                uint32_t pending = 0, pend_par = 0;
+                bool ok = true;
+                for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
+                    for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
+                        for (int kb = 0; kb < P.kblocks; ++kb) {
+                            if (!wait_bounded(smem_u32(&S.emptyB[rb.s]), rb.ph ^ 1, S.abort_flag, P.err,
+                                              P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            const uint32_t st = smem_u32(S.bring + (size_t)rb.s * S.bstage);
+                            const uint32_t bar = smem_u32(&S.fullB[rb.s]);
+                            mbar_arrive_expect_tx(bar, tx);
+                            tma_load_2d(st, &tmB_hi, kb * kKBlock, nt * P.tile_n, bar);
+                            if (split) tma_load_2d(st + b_bytes, &tmB_lo, kb * kKBlock, nt * P.tile_n, bar);
+                            pending |= 1u << rb.s;
+                            pend_par = (pend_par & ~(1u << rb.s)) | (rb.ph << rb.s);
+                            rb.next(P.sb);
                         }
-                        const uint32_t st = smem_u32(S.mring + (size_t)s * S.mstage) + 2 * kStageA;
-                        const uint32_t bar = smem_u32(&S.fullB[s]);
-                        mbar_arrive_expect_tx(bar, tx);
-                        tma_load_2d(st, &tmB_hi, kb * kKBlock, nt * P.tile_n, bar);
-                        if (split) tma_load_2d(st + b_bytes, &tmB_lo, kb * kKBlock, nt * P.tile_n, bar);
-                        pending |= 1u << s;
-                        pend_par = (pend_par & ~(1u << s)) | (ph << s);
-                        if (++s == P.sm) { s = 0; ph ^= 1; }
-                    }
-            if (!ok)
-                for (int i = 0; i < P.sm; ++i)
-                    if (pending & (1u << i))
-                        wait_bounded(smem_u32(&S.fullB[i]), (pend_par >> i) & 1, S.abort_flag, P.err, P.timeout_ns,
-                                     false);
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            const bool bf = P.mode != MODE_FP16X3;
-            const uint32_t id_full = idesc_f16(P.tile_n, bf), id_last = idesc_f16(P.tile_n_last, bf);
-            const uint32_t b_bytes = (uint32_t)P.tile_n * kRowBytes;
-            int s = 0;
-            uint32_t ph = 0, tph = 0;   // tph bit b: parity of partial b
-            int g_all = 0;
-            bool ok = true, issued = false;
-            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
-                for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
-                    const uint32_t idesc = (nt == P.ntiles_n - 1) ? id_last : id_full;
-                    for (int g = 0; g < ngroups && ok; ++g, ++g_all) {
-                        const int b = g_all & 1;
-                        if (!wait_bounded(smem_u32(&S.tempty[b]), ((tph >> b) & 1) ^ 1, S.abort_flag, P.err,
-                                          P.timeout_ns)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t d = tmem_base + (uint32_t)(b * kAccStride);
-                        const int kb0 = g * P.group, kb1 = min(P.kblocks, kb0 + P.group);
-                        for (int kb = kb0; kb < kb1; ++kb) {
-                            if (!wait_bounded(smem_u32(&S.fullA[s]), ph, S.abort_flag, P.err, P.timeout_ns) ||
-                                !wait_bounded(smem_u32(&S.fullB[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
+                if (!ok) drain(S.fullB, P.sb, pending, pend_par, S.abort_flag, P.err, P.timeout_ns);
+            }
+        } else if (warp == 1) {
+            // -------------------------------------------------------- MMA issuer
+            if (lane == 0) {
+                const bool bf = P.mode != MODE_FP16X3;
+                const uint32_t id_full = idesc_f16(P.tile_n, bf), id_last = idesc_f16(P.tile_n_last, bf);
+                const uint32_t b_bytes = (uint32_t)P.tile_n * kRowBytes;
+                Ring ra, rb;
+                uint32_t tph = 0;   // bit b: parity of TMEM partial b
+                int g_all = 0;
+                bool ok = true, issued = false;
+                for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
+                    for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
+                        const uint32_t idesc = (nt == P.ntiles_n - 1) ? id_last : id_full;
+                        for (int g = 0; g < ngroups && ok; ++g, ++g_all) {
+                            const int b = g_all & 1;
+                            if (!wait_bounded(smem_u32(&S.tempty[b]), ((tph >> b) & 1) ^ 1, S.abort_flag, P.err,
+                                              P.timeout_ns)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
-                            const uint32_t st = smem_u32(S.mring + (size_t)s * S.mstage);
-                            const uint32_t a_hi = st, a_lo = st + kStageA;
-                            const uint32_t b_hi = st + 2 * kStageA, b_lo = b_hi + b_bytes;
-#pragma unroll
-                            for (int kk = 0; kk < kKBlock / 16; ++kk) {
-                                const uint32_t ko = kk * 32;   // 16 K values = 32 bytes along the row
-                                const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-                                mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_hi + ko), idesc, acc);
-                                if (split) {
-                                    mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_lo + ko), idesc, 1u);
-                                    mma_f16(d, sdesc_k64(a_lo + ko), sdesc_k64(b_hi + ko), idesc, 1u);
+                            const uint32_t d = tmem_base + (uint32_t)(b * kAccStride);
+                            const int kb0 = g * P.group, kb1 = min(P.kblocks, kb0 + P.group);
+                            for (int kb = kb0; kb < kb1; ++kb) {
+                                if (!wait_bounded(smem_u32(&S.fullA[ra.s]), ra.ph, S.abort_flag, P.err, P.timeout_ns) ||
+                                    !wait_bounded(smem_u32(&S.fullB[rb.s]), rb.ph, S.abort_flag, P.err, P.timeout_ns)) {
+                                    ok = false;
+                                    break;
                                 }
+                                tc_fence_after();
+                                const uint32_t a_hi = smem_u32(S.aring + (size_t)ra.s * 2 * kStageA), a_lo = a_hi + kStageA;
+                                const uint32_t b_hi = smem_u32(S.bring + (size_t)rb.s * S.bstage), b_lo = b_hi + b_bytes;
+#pragma unroll
+                                for (int kk = 0; kk < kKBlock / 16; ++kk) {
+                                    const uint32_t ko = kk * 32;   // 16 K values = 32 bytes along the row
+                                    const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
+                                    mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_hi + ko), idesc, acc);
+                                    if (split) {
+                                        mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_lo + ko), idesc, 1u);
+                                        mma_f16(d, sdesc_k64(a_lo + ko), sdesc_k64(b_hi + ko), idesc, 1u);
+                                    }
+                                }
+                                issued = true;
+                                mma_commit(smem_u32(&S.emptyA[ra.s]));
+                                mma_commit(smem_u32(&S.emptyB[rb.s]));
+                                ra.next(P.sa);
+                                rb.next(P.sb);
                             }
-                            issued = true;
-                            mma_commit(smem_u32(&S.emptyM[s]));
-                            if (++s == P.sm) { s = 0; ph ^= 1; }
+                            if (!ok) break;
+                            mma_commit(smem_u32(&S.tfull[b]));
+                            tph ^= 1u << b;
                         }
-                        if (!ok) break;
-                        mma_commit(smem_u32(&S.tfull[b]));
-                        tph ^= 1u << b;
                     }
+                if (issued) {
+                    // all MMAs of this thread complete before TMEM is released
+                    mma_commit(smem_u32(S.mma_done));
+                    wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
                 }
-            if (issued) {
-                mma_commit(smem_u32(S.mma_done));
-                wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
             }
-        }
-    } else if (warp >= kConvWarp0 && warp < kConvWarp0 + kNumConvWarps) {
-        // ------------------------------------------------------------ converters
-        const int m = threadIdx.x - 32 * kConvWarp0;       // tile row 0..127
-        int sd = 0, sm = 0;
-        uint32_t phd = 0, phm = 0;
-        bool ok = true;
-        for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x) {
-            const int64_t row = mt * kTileM + m;
-            float sc = 1.0f;
-            if (P.mode == MODE_FP16X3 && P.rexp != nullptr && row < P.nlos) sc = ldexpf(1.0f, (int)P.rexp[row]);
-            for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
-                for (int kb = 0; kb < P.kblocks; ++kb) {
+        } else if (warp >= kConvWarp0) {
+            // -------------------------------------------------------- converters (first N tile only)
+            const int m = threadIdx.x - 32 * kConvWarp0;       // tile row 0..127
+            const int sw = (m >> 1) & 3;
+            Ring rd, ra;
+            bool ok = true;
+            int mt_count = 0;
+            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count) {
+                const int64_t row = mt * kTileM + m;
+                float sc = 1.0f;
+                if (P.mode == MODE_FP16X3 && P.rexp != nullptr && row < P.nlos) sc = ldexpf(1.0f, (int)P.rexp[row]);
+                const int nconv = P.reuse ? 1 : P.ntiles_n;   // N tiles whose A tiles are converted here
+                for (int kb_all = 0; kb_all < nconv * P.kblocks; ++kb_all) {
+                    const int kb = kb_all % P.kblocks;
                     float q[16], u[16];
                     const int c0 = kb * kChanPerKBlock;
                     uint32_t live;   // bit i: channel i of this K block contributes
                     if (P.layout == RMS_CHAN_MAJOR) live = (P.nk - c0 >= 16) ? 0xffffu : ((1u << (P.nk - c0)) - 1u);
                     else live = __ldg(P.kbmask + kb);
                     if (P.use_tma) {
-                        if (!warp_wait(smem_u32(&S.fullD[sd]), phd, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
-                        const float *dq = reinterpret_cast<const float *>(S.dring + (size_t)sd * 2 * kStageD);
+                        if (!warp_wait(smem_u32(&S.fullD[rd.s]), rd.ph, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                        const float *dq = reinterpret_cast<const float *>(S.dring + (size_t)rd.s * 2 * kStageD);
                         const float *du = dq + kStageD / 4;
                         if (P.layout == RMS_CHAN_MAJOR) {
                             // [16 channels][128 LOS]
@@ -519,7 +603,6 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
                             }
                         } else {
                             // [128 rows][16 channels], 64-byte swizzled
-                            const int sw = (m >> 1) & 3;
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const float4 a = *reinterpret_cast<const float4 *>(dq + m * 16 + ((c ^ sw) << 2));
@@ -528,6 +611,12 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
                                 u[4 * c] = b.x; u[4 * c + 1] = b.y; u[4 * c + 2] = b.z; u[4 * c + 3] = b.w;
                             }
                         }
+                        // the slot is refilled by TMA (async proxy): order these generic-proxy
+                        // reads before the release
+                        fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&S.emptyD[rd.s]));
+                        rd.next(P.sd);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
@@ -545,20 +634,27 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
                         if (!((live >> i) & 1u)) { q[i] = 0.f; u[i] = 0.f; }   // flagged / padding: also kills NaN
-                    if (!warp_wait(smem_u32(&S.emptyM[sm]), phm ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
-                    uint8_t *st = S.mring + (size_t)sm * S.mstage;
-                    convert_row(q, u, sc, P.mode, st, st + kStageA, m);
-                    fence_proxy_async_smem();
+                    if (!warp_wait(smem_u32(&S.emptyA[ra.s]), ra.ph ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                    uint8_t *st = S.aring + (size_t)ra.s * 2 * kStageA;
+                    // the scratch copy of this stage has the A slot's exact layout
+                    uint8_t *scr = P.reuse
+                                       ? reinterpret_cast<uint8_t *>(P.scratch + ((size_t)blockIdx.x * P.kblocks + kb) *
+                                                                                     (2 * kStageA / 16))
+                                       : nullptr;
+                    convert_row(q, u, sc, P.mode, st, st + kStageA, m, sw, scr);
+                    fence_proxy_async_all();
                     __syncwarp();
-                    if (lane == 0) {
-                        if (P.use_tma) mbar_arrive(smem_u32(&S.emptyD[sd]));
-                        mbar_arrive(smem_u32(&S.fullA[sm]));
-                    }
-                    if (P.use_tma && ++sd == P.sd) { sd = 0; phd ^= 1; }
-                    if (++sm == P.sm) { sm = 0; phm ^= 1; }
+                    if (lane == 0) mbar_arrive(smem_u32(&S.fullA[ra.s]));
+                    ra.next(P.sa);
                 }
+                if (!ok) break;
+                if (P.reuse) {
+                    // the A slots of the remaining N tiles are filled from scratch by the producer
+                    for (int i = 0; i < (P.ntiles_n - 1) * P.kblocks; ++i) ra.next(P.sa);
+                    if (lane == 0) mbar_arrive(smem_u32(&S.scr_ready[mt_count & 1]));
+                }
+            }
         }
-    }
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
         // ------------------------------------------------------------ epilogue
@@ -622,20 +718,20 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
                     }
                 }
                 if (P.F != nullptr) {
-                    // transpose 32-column chunks through shared memory so that each store
-                    // instruction writes two contiguous 128-byte row segments
+                    // transpose 16-column chunks through shared memory: each store
+                    // instruction then writes four contiguous 64-byte row segments
 #pragma unroll
-                    for (int c0 = 0; c0 < kHalf; c0 += 32) {
+                    for (int c0 = 0; c0 < kHalf; c0 += 16) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
+                        for (int j = 0; j < 16; ++j)
                             if (c0 + j < kHalf) stg[lane * kEpiLd + j] = master[c0 + j];
                         __syncwarp();
-                        const int jj = (lane & 15) * 2;
-                        const int kk = kbase + (c0 >> 1) + (lane & 15);
+                        const int jj = (lane & 7) * 2;
+                        const int kk = kbase + (c0 >> 1) + (lane & 7);
                         const bool colok = c0 + jj < min(ncols, kHalf) && kk < P.nphi;
-#pragma unroll 4
-                        for (int it = 0; it < 16; ++it) {
-                            const int r = 2 * it + (lane >> 4);
+#pragma unroll
+                        for (int it = 0; it < 8; ++it) {
+                            const int r = 4 * it + (lane >> 3);
                             const int64_t grow = mt * kTileM + 32 * q + r;
                             if (colok && grow < P.nlos) {
                                 const float2 val = make_float2(stg[r * kEpiLd + jj], stg[r * kEpiLd + jj + 1]);
@@ -751,18 +847,20 @@ bool encode_data_map(CUtensorMap *map, const float *base, int64_t nlos, int32_t 
 
 }  // namespace
 
-int umma_mstages(int tile_n, int sd)
+// Data and A rings of 3 stages each; the B ring takes the rest of shared memory.
+int umma_bstages(int tile_n, int sd, int sa)
 {
-    size_t mst = 2 * (size_t)kStageA + 2 * (size_t)tile_n * kRowBytes;
-    size_t avail = kSmemLimit - fixed_smem() - (size_t)sd * 2 * kStageD;
-    int s = (int)(avail / mst);
-    return s > 6 ? 6 : s;
+    size_t bst = 2 * (size_t)tile_n * kRowBytes;
+    size_t avail = kSmemLimit - fixed_smem() - (size_t)sd * 2 * kStageD - (size_t)sa * 2 * kStageA - 8 * 2 * (sd + sa);
+    int s = (int)(avail / (bst + 16));
+    return s > 8 ? 8 : s;
 }
 
-size_t umma_smem_bytes(int tile_n, int sd, int sm)
+size_t umma_smem_bytes(int tile_n, int sd, int sa, int sb)
 {
-    size_t mst = 2 * (size_t)kStageA + 2 * (size_t)tile_n * kRowBytes;
-    return fixed_smem() + (size_t)sd * 2 * kStageD + (size_t)sm * mst + 8 * (2 * sd + 3 * sm);
+    size_t bst = 2 * (size_t)tile_n * kRowBytes;
+    return fixed_smem() + (size_t)sd * 2 * kStageD + (size_t)sa * 2 * kStageA + (size_t)sb * bst +
+           8 * 2 * (size_t)(sd + sa + sb);
 }
 
 cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
@@ -817,6 +915,7 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
     P.rexp = P.mode == MODE_FP16X3 ? rexp : nullptr;
     P.err = p.d_err;
     P.timeout_ns = p.timeout_ns;
+    P.scratch = reinterpret_cast<uint4 *>(p.d_scratch);
 
     CUtensorMap tq, tu;
     std::memset(&tq, 0, sizeof(tq));
@@ -828,10 +927,16 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
     }();
     P.use_tma = tma_allowed && encode_data_map(&tq, Q, nlos, p.nchan, layout) &&
                 encode_data_map(&tu, U, nlos, p.nchan, layout);
-    P.sd = P.use_tma ? 4 : 0;
-    P.sm = umma_mstages(p.tile_n, P.sd);
-    if (P.sm < 2) return cudaErrorInvalidConfiguration;
-    size_t smem = umma_smem_bytes(p.tile_n, P.sd, P.sm);
+    P.sd = P.use_tma ? 3 : 0;
+    P.sa = 3;
+    P.sb = umma_bstages(p.tile_n, P.sd, P.sa);
+    // Reloading from scratch is safe when a converter's write of K block kb for the
+    // next M tile is ordered after the bulk copy that last read it: the converter
+    // waits for the A slot used sa stages earlier, which is at or after that copy's
+    // stage when kblocks >= sa.
+    P.reuse = (p.ntiles_n > 1 && P.kblocks >= P.sa && p.d_scratch != nullptr) ? 1 : 0;
+    if (P.sb < 2) return cudaErrorInvalidConfiguration;
+    size_t smem = umma_smem_bytes(p.tile_n, P.sd, P.sa, P.sb);
     cudaError_t e = cudaFuncSetAttribute(umma_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t nmt = (nlos + kTileM - 1) / kTileM;
