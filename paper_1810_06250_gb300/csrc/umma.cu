@@ -180,9 +180,14 @@ __device__ __forceinline__ void mbar_arrive_n(uint32_t bar, uint32_t n)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(n) : "memory");
 }
-// Orders this thread's generic-proxy accesses (shared and global) before later
-// async-proxy accesses (TMA, tensor core).
-__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// Orders this thread's generic-proxy global accesses before later async-proxy
+// accesses (bulk copies reading what it wrote).
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// Hint: bring [addr, addr + bytes) into L2 (16-byte aligned, multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void *addr, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(addr), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -301,6 +306,7 @@ struct Smem {
         *mma_done;
     uint32_t *tmem_slot;
     volatile int *abort_flag;
+    int *converted;     // converter warps done with their M tiles' first N tile (x4 per M tile)
 };
 
 __device__ __forceinline__ Smem carve(uint8_t *base, const UmmaParams &P)
@@ -328,6 +334,7 @@ __device__ __forceinline__ Smem carve(uint8_t *base, const UmmaParams &P)
     s.mma_done = s.scr_ready + 2;
     s.tmem_slot = reinterpret_cast<uint32_t *>(s.mma_done + 1);
     s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
+    s.converted = const_cast<int *>(s.abort_flag) + 1;
     return s;
 }
 
@@ -391,6 +398,7 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
         }
         mbar_init(smem_u32(S.mma_done), 1);
         *S.abort_flag = 0;
+        *S.converted = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -571,6 +579,46 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
                     wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
                 }
             }
+        } else if (warp == 3) {
+            // -------------------------------------------------------- L2 prefetcher
+            // Once the converters have finished an M tile's first N tile, its FP32 input
+            // is no longer needed and the next M tile's input is prefetched into L2, so
+            // that the next first N tile streams from L2 instead of waiting on HBM:
+            // channel-major: 512-byte row pieces (Q and U of every active channel),
+            // LOS-major: the contiguous 128-row blocks of Q and U in 4 KB pieces.
+            if (P.reuse && P.use_tma) {
+                const int units = P.layout == RMS_CHAN_MAJOR ? 2 * P.nk
+                                                             : 2 * (int)(((int64_t)kTileM * P.nchan * 4 + 4095) / 4096);
+                int mt_count = 0;
+                for (int64_t mt = blockIdx.x; mt + gridDim.x < nmt; mt += gridDim.x, ++mt_count) {
+                    // a pure performance hint: on a stall or an abort, stop prefetching
+                    const uint64_t t0 = global_ns();
+                    bool go = true;
+                    while (go && *reinterpret_cast<volatile int *>(S.converted) < kNumConvWarps * (mt_count + 1)) {
+                        __nanosleep(256);
+                        go = !*S.abort_flag && (int64_t)(global_ns() - t0) < P.timeout_ns / 4;
+                    }
+                    if (!__all_sync(0xffffffffu, go)) break;
+                    const int64_t mn = mt + gridDim.x;
+                    const int64_t rows = min((int64_t)kTileM, P.nlos - mn * kTileM);
+                    for (int u = lane; u < units; u += 32) {
+                        if (P.layout == RMS_CHAN_MAJOR) {
+                            const float *src = (u & 1) ? P.U : P.Q;
+                            const int64_t off = (int64_t)__ldg(P.active + (u >> 1)) * P.nlos + mn * kTileM;
+                            prefetch_l2(src + off, (uint32_t)(rows * 4));
+                        } else {
+                            const int per = units / 2;
+                            const int64_t b0 = (int64_t)(u % per) * 4096;
+                            const int64_t avail = rows * P.nchan * 4 - b0;
+                            if (avail > 0) {
+                                const char *src = reinterpret_cast<const char *>((u / per) ? P.U : P.Q) +
+                                                  mn * kTileM * P.nchan * 4 + b0;
+                                prefetch_l2(src, (uint32_t)min((int64_t)4096, avail));
+                            }
+                        }
+                    }
+                }
+            }
         } else if (warp >= kConvWarp0) {
             // -------------------------------------------------------- converters (first N tile only)
             const int m = threadIdx.x - 32 * kConvWarp0;       // tile row 0..127
@@ -642,16 +690,22 @@ umma_synth_kernel(const __grid_constant__ UmmaParams P, const __grid_constant__ 
                                                                                      (2 * kStageA / 16))
                                        : nullptr;
                     convert_row(q, u, sc, P.mode, st, st + kStageA, m, sw, scr);
-                    fence_proxy_async_all();
+                    fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&S.fullA[ra.s]));
                     ra.next(P.sa);
                 }
                 if (!ok) break;
                 if (P.reuse) {
-                    // the A slots of the remaining N tiles are filled from scratch by the producer
+                    // the A slots of the remaining N tiles are filled from scratch by the
+                    // producer's bulk copies: make the scratch writes visible to them
                     for (int i = 0; i < (P.ntiles_n - 1) * P.kblocks; ++i) ra.next(P.sa);
-                    if (lane == 0) mbar_arrive(smem_u32(&S.scr_ready[mt_count & 1]));
+                    fence_proxy_async_global();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(smem_u32(&S.scr_ready[mt_count & 1]));
+                        atomicAdd(S.converted, 1);
+                    }
                 }
             }
         }
@@ -816,7 +870,7 @@ __global__ void row_exponent_kernel(const float *__restrict__ Q, const float *__
     }
 }
 
-size_t fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 8 + 8 * 32 + 16; }
+size_t fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 8 + 8 * 32 + 32; }
 
 bool encode_data_map(CUtensorMap *map, const float *base, int64_t nlos, int32_t nchan, int layout)
 {
