@@ -24,9 +24,12 @@
  *    by rms_plan_sync and by the next rms_synth on that plan.
  *  - Nothing in the library calls exit(), abort() or a device trap.
  *  - Units: lambda^2 in m^2, frequency in Hz, phi in rad m^-2.
- *  - A plan may be used from several streams at once: it is read-only after
- *    creation, except rms_synth_host, which owns per-plan staging buffers and
- *    must not run concurrently with itself on one plan.
+ *  - A plan may be used from several streams.  The tensor-core precisions keep
+ *    a per-plan scratch for split operands, so every synthesis call on a plan
+ *    waits on the device for the previous call on that plan (an event recorded
+ *    by each call); use one plan per stream for concurrent work.
+ *    rms_synth_host owns per-plan staging buffers and must not run
+ *    concurrently with itself on one plan.
  */
 #ifndef RMS_H
 #define RMS_H
@@ -127,7 +130,10 @@ rms_status rms_rmsf(rms_plan_t plan, float *R_out, double *lambda0sq, double *K,
  *  stream    cudaStream_t as void*.
  * |F| is sqrt(re*re + im*im) of the stored FP32 values, each product and the sum
  * rounded to FP32 separately, so the peak index can be recomputed bit-exactly
- * from F_out.  Asynchronous; performs no allocation and no host sync.
+ * from F_out.  Asynchronous, no host sync.  FP16X3 plans take a one-byte-per-LOS
+ * exponent scratch from the device's stream-ordered memory pool on `stream`
+ * (cudaMallocAsync / cudaFreeAsync) for each call; the other precisions
+ * allocate nothing.
  */
 rms_status rms_synth(rms_plan_t plan, const float *Q, const float *U, int64_t nlos, int32_t layout,
                      float *F_out, int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream);
