@@ -68,5 +68,5 @@ class Plan:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    from .build import build as _b
+    from .builder import build as _b
     return _b(force=force, verbose=verbose)

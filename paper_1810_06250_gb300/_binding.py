@@ -54,7 +54,7 @@ def load(path: str = LIB_PATH):
         if _lib is not None:
             return _lib
         if not os.path.exists(path):
-            raise RuntimeError("librms.so is not built (%s); run paper_1810_06250_gb300.build.build()" % path)
+            raise RuntimeError("librms.so is not built (%s); run paper_1810_06250_gb300.build()" % path)
         lib = ctypes.CDLL(path)
         P = _c_void_p
         sig = {
