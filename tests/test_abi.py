@@ -16,7 +16,7 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1810_06250_gb300.build import build
+    from paper_1810_06250_gb300.builder import build
     path = build()
     return ctypes.CDLL(path)
 
