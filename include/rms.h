@@ -149,6 +149,30 @@ rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64
                           int32_t layout, float *F_out, int32_t *peak_idx, float *peak_abs,
                           float *phi_peak, void *stream);
 
+/*
+ * rms_synth for FP16X3 plans that allocates nothing.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory while
+ * they process data -- a pipeline that reserves all of its GPU memory when an
+ * observation starts and treats any later allocation as an error, or a host
+ * framework whose own allocator owns the device's memory budget.  rms_synth on
+ * an FP16X3 plan takes a one-byte-per-LOS scratch from the stream-ordered pool
+ * for every call; here that scratch is a fixed device array of
+ * RMS_NOALLOC_MAX_LOS bytes compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * Same arguments and results as rms_synth.  Returns RMS_ERR_INVALID_ARG when
+ * nlos > RMS_NOALLOC_MAX_LOS (nothing is launched) and RMS_ERR_UNSUPPORTED for a
+ * plan of another precision (rms_synth allocates nothing for those already).
+ * Calls no cudaMalloc, cudaFree or pool allocation.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls in the process share the one
+ * array and every call rewrites the entries it uses, so calls whose kernels
+ * overlap on the GPU race: do not run two at once, on any plans or streams.
+ */
+#define RMS_NOALLOC_MAX_LOS (1 << 22)
+rms_status rms_synth_noalloc(rms_plan_t plan, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                             float *F_out, int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream);
+
 /* Wait for `stream` (void* cudaStream_t) and report sticky device errors of
  * this plan: RMS_ERR_TIMEOUT if a kernel's bounded wait gave up, RMS_ERR_CUDA
  * for an asynchronous CUDA error.  The sticky state is cleared by the call. */

@@ -30,9 +30,10 @@ PRECISIONS = {"fp32_fly": RMS_FP32_SIMT_FLY, "fp32_table": RMS_FP32_SIMT_TABLE, 
 LAYOUTS = {"chan": RMS_CHAN_MAJOR, "los": RMS_LOS_MAJOR}
 
 # Every symbol include/rms.h declares (checked by the ABI test).
-EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_plan_sync",
-           "rms_plan_info", "rms_plan_get", "rms_plan_destroy", "rms_status_string",
+EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_synth_noalloc",
+           "rms_plan_sync", "rms_plan_info", "rms_plan_get", "rms_plan_destroy", "rms_status_string",
            "rms_plan_set_timeout")
+RMS_NOALLOC_MAX_LOS = 1 << 22
 
 
 class RmsError(RuntimeError):
@@ -62,6 +63,7 @@ def load(path: str = LIB_PATH):
             "rms_rmsf": [P, P, P, P, P, P],
             "rms_synth": [P, P, P, _i64, _i32, P, P, P, P, P],
             "rms_synth_host": [P, P, P, _i64, _i32, P, P, P, P, P],
+            "rms_synth_noalloc": [P, P, P, _i64, _i32, P, P, P, P, P],
             "rms_plan_sync": [P, P],
             "rms_plan_info": [P, _i32, P],
             "rms_plan_get": [P, _i32, P, _i64],
@@ -172,6 +174,20 @@ def rms_synth(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None, pea
                           _dptr(peak_idx, torch.int32, "peak_idx"), _dptr(peak_abs, torch.float32, "peak_abs"),
                           _dptr(phi_peak, torch.float32, "phi_peak"), _stream(stream))
     _check(st, "rms_synth")
+
+
+def rms_synth_noalloc(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None, peak_abs=None,
+                      phi_peak=None, stream=None):
+    """rms_synth for FP16X3 plans with a fixed scratch array instead of a per-call
+    pool allocation, for callers that must not allocate device memory while they
+    process data (see include/rms.h: at most RMS_NOALLOC_MAX_LOS lines of sight,
+    calls must not overlap on the GPU)."""
+    import torch
+    st = load().rms_synth_noalloc(plan, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                                  _layout(layout), _dptr(F_out, None, "F_out"),
+                                  _dptr(peak_idx, torch.int32, "peak_idx"), _dptr(peak_abs, torch.float32, "peak_abs"),
+                                  _dptr(phi_peak, torch.float32, "phi_peak"), _stream(stream))
+    _check(st, "rms_synth_noalloc")
 
 
 def rms_synth_host(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None, peak_abs=None,

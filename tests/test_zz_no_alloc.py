@@ -1,0 +1,74 @@
+"""rms_synth_noalloc: the FP16X3 synthesis entry point that allocates nothing.
+
+It exists for callers that cannot allocate device memory while they process
+data (memory reserved up front, or owned by another allocator).  Its results
+must match rms_synth's on the same plan, call after call, although every call
+reuses the same fixed scratch array.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+import gpu_helpers as gh
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1810_06250_gb300 as rms
+    rms.build()
+    rms.load()
+    return rms
+
+
+def _outputs(nlos, nphi):
+    dev = torch.device("cuda")
+    return (torch.full((nlos, nphi, 2), float("nan"), device=dev),
+            torch.full((nlos,), -7, dtype=torch.int32, device=dev),
+            torch.zeros(nlos, device=dev), torch.zeros(nlos, device=dev))
+
+
+@pytest.mark.parametrize("layout", ["chan", "los"])
+def test_noalloc_matches_rms_synth(rms, layout):
+    from paper_1810_06250_gb300 import inputs
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
+    nlos = 20000
+    dev = torch.device("cuda")
+    with rms.Plan(freq, phi, "fp16x3", weights=w) as plan:
+        for call, start in enumerate((0, 50000)):     # two calls in a row, different cubes
+            Q, U = inputs.make_cube(cfg, start, nlos)
+            if call == 1:
+                Q *= 37.5                               # other per-LOS exponents than the first call
+                U *= 37.5
+            q = torch.from_numpy(inputs.to_layout(Q, layout)).to(dev)
+            u = torch.from_numpy(inputs.to_layout(U, layout)).to(dev)
+            F0, i0, a0, p0 = _outputs(nlos, cfg.nphi)
+            F1, i1, a1, p1 = _outputs(nlos, cfg.nphi)
+            rms.rms_synth(plan.handle, q, u, nlos, layout, F0, i0, a0, p0)
+            rms.rms_synth_noalloc(plan.handle, q, u, nlos, layout, F1, i1, a1, p1)
+            plan.sync()
+            Fa, Fb = F0.cpu().numpy(), F1.cpu().numpy()
+            per, _ = gh.errors(Fb[..., 0] + 1j * Fb[..., 1], Fa[..., 0] + 1j * Fa[..., 1])
+            assert per.max() <= gh.TOL["fp16x3"], per.max()
+            np.testing.assert_array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+            np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+            np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+
+
+def test_noalloc_limits(rms):
+    from paper_1810_06250_gb300 import inputs
+    cfg = inputs.CONFIGS["tiny"]
+    freq, phi = inputs.frequencies(cfg), inputs.phi_grid(cfg)
+    q = torch.zeros(cfg.nchan * 8, device="cuda")
+    with rms.Plan(freq, phi, "fp16x3") as plan:
+        with pytest.raises(rms.RmsError) as e:       # beyond the fixed scratch: rejected, nothing launched
+            rms.rms_synth_noalloc(plan.handle, q, q, rms.RMS_NOALLOC_MAX_LOS + 1, "chan", None, q.view(torch.int32))
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+    with rms.Plan(freq, phi, "bf16x3") as plan:
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_synth_noalloc(plan.handle, q, q, 8, "chan", None, q.view(torch.int32))
+        assert e.value.status == rms.RMS_ERR_UNSUPPORTED
