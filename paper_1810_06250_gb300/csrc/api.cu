@@ -276,7 +276,15 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
         RMS_TRY(launch_phase_table(*p, 0));
     } else if (is_tensor(precision)) {
         const int N = 2 * nphi;
-        p->ntiles_n = (N + kMaxTileN - 1) / kMaxTileN;
+        // RMS_MAX_TILE_N (16..208, multiple of 16) in the environment lowers the phase
+        // rows per tensor-core tile (a tuning knob: smaller tiles leave shared memory
+        // for more pipeline stages)
+        int max_tile = kMaxTileN;
+        if (const char *v = std::getenv("RMS_MAX_TILE_N")) {
+            int t = std::atoi(v);
+            if (t >= 16 && t <= kMaxTileN && t % 16 == 0) max_tile = t;
+        }
+        p->ntiles_n = (N + max_tile - 1) / max_tile;
         int per = (N + p->ntiles_n - 1) / p->ntiles_n;
         p->tile_n = (per + 15) / 16 * 16;
         int last = N - (p->ntiles_n - 1) * p->tile_n;
@@ -322,6 +330,16 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
         }
     }
     RMS_TRY(cudaEventCreateWithFlags(&p->last, cudaEventDisableTiming));
+    if (is_tensor(precision)) {
+        // rms_synth takes per-call scratch from the device's default stream-ordered
+        // pool; keep freed blocks reserved there so calls do not go back to the driver
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     RMS_TRY(launch_rmsf(*p, p->d_phi, nphi, p->d_R64, nullptr, 0));
     RMS_TRY(cudaDeviceSynchronize());
     p->fwhm_meas = measure_fwhm(p);
@@ -387,16 +405,19 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
         break;
     case RMS_BF16:
     case RMS_BF16X3:
-        e = launch_umma(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, nullptr, s);
-        break;
     case RMS_FP16X3: {
-        // per-LOS exponents: stream-ordered scratch of nlos bytes
-        int8_t *rexp = nullptr;
-        e = cudaMallocAsync(reinterpret_cast<void **>(&rexp), (size_t)nlos, s);
-        if (e != cudaSuccess) return from_cuda(e);
-        e = launch_row_exponent(*p, Q, U, nlos, layout, rexp, s);
-        if (e == cudaSuccess) e = launch_umma(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, rexp, s);
-        cudaError_t e2 = cudaFreeAsync(rexp, s);
+        // the split operand (and FP16X3's per-LOS exponents): stream-ordered scratch
+        const size_t abytes = split_operand_bytes(*p, nlos, layout);
+        const size_t rbytes = p->precision == RMS_FP16X3 ? (size_t)((nlos + 255) & ~(int64_t)255) : 0;
+        uint8_t *scr = nullptr;
+        e = cudaMallocAsync(reinterpret_cast<void **>(&scr), abytes + rbytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return from_cuda(e);
+        }
+        e = launch_split_gemm(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, scr,
+                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s);
+        cudaError_t e2 = cudaFreeAsync(scr, s);
         if (e == cudaSuccess) e = e2;
         break;
     }

@@ -1,0 +1,554 @@
+// Tensor-core RM synthesis in two kernels: a streaming split of the cube into
+// 16-bit operands, then a tcgen05 contraction that only moves tiles.
+//
+// split_kernel (the layout stage): one CTA per 128-LOS M tile, one thread per
+// LOS.  It reads FP32 Q/U in either cube layout once, zeroes flagged and padding
+// channels (killing NaN there), and writes each K block of 16 channels as the
+// exact shared-memory image the MMA reads: 128 rows x 64 bytes of hi parts, then
+// of lo parts, 16-byte chunks swizzled in 64-byte rows (chunk c of row m at
+// m * 64 + ((c ^ ((m >> 1) & 3)) << 4)).  For FP16X3 it first finds the row's
+// largest |value| and stores the power-of-two exponent that brings it into
+// [2^14, 2^15).
+//
+// gemm_kernel: C[l][2k + {0,1}] = sum over K of A[l][.] B[2k + {0,1}][.] with the
+// phase matrix B of phase.cu (see umma.cu for the real form of Eq. Fsum).  A CTA
+// is persistent over 128-row M tiles and runs each M tile's N tiles in order.
+//   warp 0      producer: one bulk copy of the split A stage and TMA of the B hi/lo
+//               tiles per stage                                   -> full
+//   warp 1      TMEM allocator, single-thread MMA issuer          -> empty, tfull
+//   warp 2      L2 prefetch of the next M tile's operand
+//   warps 4-11  epilogue: warp w owns TMEM lane quarter w % 4 and column half
+//               (w - 4) / 4; folds partials, scales, peak, stores F  -> tempty
+// MMAs run in groups of a few K blocks into one of two TMEM partials and the
+// epilogue folds each partial into FP32 registers with round-to-nearest adds,
+// because the tensor core's own FP32 accumulation does not round to nearest.
+// Every wait is bounded: a wait that runs out aborts the CTA, records
+// RMS_DEVERR_TIMEOUT, drains in-flight copies and MMAs and frees TMEM.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <limits.h>
+
+#include <cstring>
+
+#include "rms_internal.h"
+
+namespace {
+
+#include "tc_ptx.cuh"
+
+constexpr int kThreads = 384;
+constexpr int kEpiWarp0 = 4, kNumEpiWarps = 8;
+constexpr int kRowBytes = kKBlock * 2;            // 64 B per operand row per stage
+constexpr int kStageA = kTileM * kRowBytes;       // 8 KB per A part
+constexpr int kTmemCols = 512;
+constexpr int kAccStride = 256;
+constexpr int kHalf = kMaxTileN / 2;              // 104 columns per epilogue thread
+constexpr int kEpiLd = 17;
+constexpr int kEpiStageBytes = kNumEpiWarps * 32 * kEpiLd * 4;
+constexpr int kSmemLimit = 227 * 1024;
+
+enum { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_FP16X3 = 2 };
+
+// ----------------------------------------------------------------------------
+// split_kernel
+// ----------------------------------------------------------------------------
+struct SplitParams {
+    const float *Q, *U;
+    int64_t nlos;
+    int32_t nchan, layout, nk, kblocks, mode;
+    int32_t vec4;               // LOS-major rows are 16-byte aligned: vector loads
+    const int32_t *active;      // channel-major: active channel list
+    const uint16_t *kbmask;     // LOS-major: per K block, bit i = channel 16 kb + i active
+    uint8_t *A;                 // [nmt][kblocks][16 KB]
+    int8_t *rexp;               // [nlos] (FP16X3)
+};
+
+__device__ __forceinline__ void load_kblock(const SplitParams &P, int64_t row, int kb, float (&q)[16], float (&u)[16])
+{
+    const int c0 = kb * kChanPerKBlock;
+    if (P.layout == RMS_CHAN_MAJOR) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            q[i] = 0.f;
+            u[i] = 0.f;
+            if (c0 + i < P.nk && row < P.nlos) {
+                const int64_t off = (int64_t)__ldg(P.active + c0 + i) * P.nlos + row;
+                q[i] = __ldg(P.Q + off);
+                u[i] = __ldg(P.U + off);
+            }
+        }
+    } else {
+        const uint32_t live = __ldg(P.kbmask + kb);
+        if (P.vec4 && row < P.nlos && c0 + 16 <= P.nchan) {
+            // 16 contiguous channels of this row: four 16-byte loads per array
+            const float4 *q4 = reinterpret_cast<const float4 *>(P.Q + row * P.nchan + c0);
+            const float4 *u4 = reinterpret_cast<const float4 *>(P.U + row * P.nchan + c0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 a = __ldg(q4 + v), b = __ldg(u4 + v);
+                q[4 * v] = a.x; q[4 * v + 1] = a.y; q[4 * v + 2] = a.z; q[4 * v + 3] = a.w;
+                u[4 * v] = b.x; u[4 * v + 1] = b.y; u[4 * v + 2] = b.z; u[4 * v + 3] = b.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (!((live >> i) & 1u)) { q[i] = 0.f; u[i] = 0.f; }   // flagged: also kills NaN
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                q[i] = 0.f;
+                u[i] = 0.f;
+                if (((live >> i) & 1u) && row < P.nlos) {
+                    q[i] = __ldg(P.Q + row * P.nchan + c0 + i);
+                    u[i] = __ldg(P.U + row * P.nchan + c0 + i);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
+{
+    const int m = threadIdx.x;
+    const int64_t mt = blockIdx.x;
+    const int64_t row = mt * kTileM + m;
+    const int sw = (m >> 1) & 3;
+    float scale = 1.0f;
+    if (P.mode == MODE_FP16X3) {
+        float mx = 0.f;
+        for (int kb = 0; kb < P.kblocks; ++kb) {
+            float q[16], u[16];
+            load_kblock(P, row, kb, q, u);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(q[i]), fabsf(u[i])));
+        }
+        int e = 0;
+        if (mx > 0.f && isfinite(mx)) { frexpf(mx, &e); e = 15 - e; }
+        e = max(-100, min(100, e));
+        scale = ldexpf(1.0f, e);
+        if (row < P.nlos) P.rexp[row] = (int8_t)e;
+    }
+    uint8_t *dst = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
+    for (int kb = 0; kb < P.kblocks; ++kb, dst += 2 * kStageA) {
+        float q[16], u[16];
+        load_kblock(P, row, kb, q, u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = 4 * c + j;
+                if (P.mode == MODE_FP16X3) split_pair_fp16(q[i] * scale, u[i] * scale, hi[j], lo[j]);
+                else split_pair_bf16(q[i], u[i], hi[j], lo[j]);
+            }
+            const uint32_t off = (uint32_t)m * kRowBytes + ((uint32_t)(c ^ sw) << 4);
+            *reinterpret_cast<uint4 *>(dst + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            if (P.mode != MODE_BF16)
+                *reinterpret_cast<uint4 *>(dst + kStageA + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// gemm_kernel
+// ----------------------------------------------------------------------------
+struct GemmParams {
+    const uint8_t *A;           // split operand, [nmt][kblocks][16 KB]
+    int64_t nlos;
+    int32_t kblocks, group;
+    int32_t nphi, ntiles_n, tile_n, tile_n_last;
+    float *F;
+    int32_t *pidx;
+    float *pabs, *pphi;
+    const float *phi32;
+    float out_scale;
+    int32_t mode;
+    const int8_t *rexp;
+    int *err;
+    int64_t timeout_ns;
+    int32_t stages;
+};
+
+struct GSmem {
+    uint8_t *ring;
+    uint32_t stage_bytes;
+    float *epi, *pk_m;
+    int *pk_i;
+    uint64_t *full, *empty, *tfull, *tempty, *pkfull, *pkempty, *mma_done;
+    uint32_t *tmem_slot;
+    volatile int *abort_flag;
+    volatile int *mt_started;   // M tiles the producer has started (read by the L2 prefetcher)
+};
+
+__device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
+{
+    GSmem s;
+    s.stage_bytes = 2 * kStageA + 2 * (uint32_t)P.tile_n * kRowBytes;
+    s.ring = base;
+    s.epi = reinterpret_cast<float *>(s.ring + (size_t)P.stages * s.stage_bytes);
+    s.pk_m = s.epi + kEpiStageBytes / 4;
+    s.pk_i = reinterpret_cast<int *>(s.pk_m + 2 * 4 * 32);
+    uint64_t *b = reinterpret_cast<uint64_t *>(s.pk_i + 2 * 4 * 32);
+    s.full = b;
+    s.empty = s.full + P.stages;
+    s.tfull = s.empty + P.stages;
+    s.tempty = s.tfull + 2;
+    s.pkfull = s.tempty + 2;
+    s.pkempty = s.pkfull + 8;
+    s.mma_done = s.pkempty + 8;
+    s.tmem_slot = reinterpret_cast<uint32_t *>(s.mma_done + 1);
+    s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
+    s.mt_started = s.abort_flag + 1;
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtensorMap tmB_hi,
+            const __grid_constant__ CUtensorMap tmB_lo)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const GSmem S = gcarve(base, P);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nmt = (P.nlos + kTileM - 1) / kTileM;
+    const bool split = P.mode != MODE_BF16;
+    const int ngroups = (P.kblocks + P.group - 1) / P.group;
+    const uint32_t a_bytes = split ? 2 * kStageA : kStageA;
+    const uint32_t b_bytes = (uint32_t)P.tile_n * kRowBytes;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.stages; ++s) {
+            mbar_init(smem_u32(&S.full[s]), 1);
+            mbar_init(smem_u32(&S.empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&S.tfull[b]), 1);
+            mbar_init(smem_u32(&S.tempty[b]), kNumEpiWarps);
+        }
+        for (int i = 0; i < 8; ++i) {
+            mbar_init(smem_u32(&S.pkfull[i]), 1);
+            mbar_init(smem_u32(&S.pkempty[i]), 1);
+        }
+        mbar_init(smem_u32(S.mma_done), 1);
+        *S.abort_flag = 0;
+        *S.mt_started = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        __syncwarp();
+        tmem_alloc(smem_u32(S.tmem_slot), kTmemCols);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *S.tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_lo)) : "memory");
+            const uint32_t tx = a_bytes + (split ? 2 * b_bytes : b_bytes);
+            int s = 0;
+            uint32_t ph = 0, pending = 0, pend_par = 0;
+            bool ok = true;
+            int mt_count = 0;
+            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count) {
+                *S.mt_started = mt_count + 1;
+                const uint8_t *a_mt = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
+                for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
+                    for (int kb = 0; kb < P.kblocks; ++kb) {
+                        if (!wait_bounded(smem_u32(&S.empty[s]), ph ^ 1, S.abort_flag, P.err, P.timeout_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t st = smem_u32(S.ring + (size_t)s * S.stage_bytes);
+                        const uint32_t bar = smem_u32(&S.full[s]);
+                        mbar_arrive_expect_tx(bar, tx);
+                        bulk_load(st, a_mt + (size_t)kb * (2 * kStageA), a_bytes, bar);
+                        tma_load_2d(st + 2 * kStageA, &tmB_hi, kb * kKBlock, nt * P.tile_n, bar);
+                        if (split) tma_load_2d(st + 2 * kStageA + b_bytes, &tmB_lo, kb * kKBlock, nt * P.tile_n, bar);
+                        pending |= 1u << s;
+                        pend_par = (pend_par & ~(1u << s)) | (ph << s);
+                        if (++s == P.stages) { s = 0; ph ^= 1; }
+                    }
+            }
+            if (!ok)
+                for (int i = 0; i < P.stages; ++i)
+                    if (pending & (1u << i))
+                        wait_bounded(smem_u32(&S.full[i]), (pend_par >> i) & 1, S.abort_flag, P.err, P.timeout_ns,
+                                     false);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const bool bf = P.mode != MODE_FP16X3;
+            const uint32_t id_full = idesc_f16(P.tile_n, bf), id_last = idesc_f16(P.tile_n_last, bf);
+            int s = 0;
+            uint32_t ph = 0, tph = 0;
+            int g_all = 0;
+            bool ok = true, issued = false;
+            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
+                for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
+                    const uint32_t idesc = (nt == P.ntiles_n - 1) ? id_last : id_full;
+                    for (int g = 0; g < ngroups && ok; ++g, ++g_all) {
+                        const int b = g_all & 1;
+                        if (!wait_bounded(smem_u32(&S.tempty[b]), ((tph >> b) & 1) ^ 1, S.abort_flag, P.err,
+                                          P.timeout_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem_base + (uint32_t)(b * kAccStride);
+                        const int kb0 = g * P.group, kb1 = min(P.kblocks, kb0 + P.group);
+                        for (int kb = kb0; kb < kb1; ++kb) {
+                            if (!wait_bounded(smem_u32(&S.full[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t st = smem_u32(S.ring + (size_t)s * S.stage_bytes);
+                            const uint32_t a_hi = st, a_lo = st + kStageA;
+                            const uint32_t b_hi = st + 2 * kStageA, b_lo = b_hi + b_bytes;
+#pragma unroll
+                            for (int kk = 0; kk < kKBlock / 16; ++kk) {
+                                const uint32_t ko = kk * 32;
+                                const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
+                                mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_hi + ko), idesc, acc);
+                                if (split) {
+                                    mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_lo + ko), idesc, 1u);
+                                    mma_f16(d, sdesc_k64(a_lo + ko), sdesc_k64(b_hi + ko), idesc, 1u);
+                                }
+                            }
+                            issued = true;
+                            mma_commit(smem_u32(&S.empty[s]));
+                            if (++s == P.stages) { s = 0; ph ^= 1; }
+                        }
+                        if (!ok) break;
+                        mma_commit(smem_u32(&S.tfull[b]));
+                        tph ^= 1u << b;
+                    }
+                }
+            if (issued) {
+                mma_commit(smem_u32(S.mma_done));
+                wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------ L2 prefetcher
+        // When the producer starts an M tile, bring the next M tile's split operand
+        // (one contiguous block) into L2 so its first N tile does not wait on HBM.
+        // A performance hint only: on a stall or an abort it stops.
+        const size_t blk = (size_t)P.kblocks * (2 * kStageA);
+        int mt_count = 0;
+        for (int64_t mt = blockIdx.x; mt + gridDim.x < nmt; mt += gridDim.x, ++mt_count) {
+            const uint64_t t0 = global_ns();
+            bool go = true;
+            while (go && *S.mt_started < mt_count + 1) {
+                __nanosleep(256);
+                go = !*S.abort_flag && (int64_t)(global_ns() - t0) < P.timeout_ns / 4;
+            }
+            if (!__all_sync(0xffffffffu, go)) break;
+            const uint8_t *nxt = P.A + (size_t)(mt + gridDim.x) * blk;
+            for (size_t off = (size_t)lane * 4096; off < blk; off += 32 * 4096)
+                prefetch_l2(nxt + off, (uint32_t)min((size_t)4096, blk - off));
+        }
+    } else if (warp >= kEpiWarp0) {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;
+        const int h = (warp - kEpiWarp0) >> 2;
+        float *stg = S.epi + (warp - kEpiWarp0) * 32 * kEpiLd;
+        const int64_t row_pitch = 2 * (int64_t)P.nphi;
+        uint32_t tph = 0;
+        int g_all = 0, mt_count = 0;
+        bool ok = true;
+        float master[kHalf];
+        for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count) {
+            const int64_t row = mt * kTileM + 32 * q + lane;
+            float scale = P.out_scale;
+            if (P.rexp != nullptr && row < P.nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
+            float bm = -1.0f;
+            int bi = INT_MAX;
+            for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
+                for (int g = 0; g < ngroups; ++g, ++g_all) {
+                    const int b = g_all & 1;
+                    if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tph ^= 1u << b;
+                    tc_fence_after();
+                    const uint32_t taddr =
+                        tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kAccStride + h * kHalf);
+#pragma unroll
+                    for (int c0 = 0; c0 < kHalf; c0 += 32) {
+                        uint32_t r[4][8];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (c0 + 8 * j < kHalf) tmem_ld8(taddr + c0 + 8 * j, r[j]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                if (c0 + 8 * j < kHalf) {
+                                    const float v = __uint_as_float(r[j][e]);
+                                    master[c0 + 8 * j + e] = g == 0 ? v : __fadd_rn(master[c0 + 8 * j + e], v);
+                                }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
+                }
+                if (!ok) break;
+                const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * kHalf;
+                const int kbase = (nt * P.tile_n + h * kHalf) >> 1;
+#pragma unroll
+                for (int p = 0; p < kHalf / 2; ++p) {
+                    const float fr = master[2 * p] * scale, fi = master[2 * p + 1] * scale;
+                    master[2 * p] = fr;
+                    master[2 * p + 1] = fi;
+                    const int k = kbase + p;
+                    if (2 * p < ncols && k < P.nphi) {
+                        const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
+                        if (m2 > bm) { bm = m2; bi = k; }
+                    }
+                }
+                if (P.F != nullptr) {
+#pragma unroll
+                    for (int c0 = 0; c0 < kHalf; c0 += 16) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < kHalf) stg[lane * kEpiLd + j] = master[c0 + j];
+                        __syncwarp();
+                        const int jj = (lane & 7) * 2;
+                        const int kk = kbase + (c0 >> 1) + (lane & 7);
+                        const bool colok = c0 + jj < min(ncols, kHalf) && kk < P.nphi;
+#pragma unroll
+                        for (int it = 0; it < 8; ++it) {
+                            const int r = 4 * it + (lane >> 3);
+                            const int64_t grow = mt * kTileM + 32 * q + r;
+                            if (colok && grow < P.nlos) {
+                                const float2 val = make_float2(stg[r * kEpiLd + jj], stg[r * kEpiLd + jj + 1]);
+                                // streaming store: F is written once and must not push the
+                                // operands out of L2
+                                __stcs(reinterpret_cast<float2 *>(P.F + grow * row_pitch + 2 * (int64_t)kk), val);
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+            if (!ok) break;
+            // combine the two column halves of each row: half 1 publishes, half 0 writes
+            const int par = mt_count & 1;
+            const uint32_t pbar = smem_u32(&S.pkfull[par * 4 + q]);
+            const uint32_t ebar = smem_u32(&S.pkempty[par * 4 + q]);
+            const uint32_t use_par = (mt_count >> 1) & 1;
+            if (h == 1) {
+                if (!warp_wait(ebar, use_par ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                S.pk_m[(par * 4 + q) * 32 + lane] = bm;
+                S.pk_i[(par * 4 + q) * 32 + lane] = bi;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(pbar);
+            } else {
+                if (!warp_wait(pbar, use_par, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                const float om = S.pk_m[(par * 4 + q) * 32 + lane];
+                const int oi = S.pk_i[(par * 4 + q) * 32 + lane];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ebar);
+                if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; }
+                if (row < P.nlos) {
+                    const bool found = bi != INT_MAX;
+                    if (P.pidx) P.pidx[row] = found ? bi : -1;
+                    if (P.pabs) P.pabs[row] = found ? sqrtf(bm) : __int_as_float(0x7fc00000);
+                    if (P.pphi) P.pphi[row] = found ? P.phi32[bi] : __int_as_float(0x7fc00000);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+size_t gemm_fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 8 + 8 * 32 + 32; }
+
+int gemm_stages(int tile_n)
+{
+    size_t st = 2 * (size_t)kStageA + 2 * (size_t)tile_n * kRowBytes;
+    int s = (int)((kSmemLimit - gemm_fixed_smem()) / (st + 16));
+    return s > 8 ? 8 : s;
+}
+
+}  // namespace
+
+size_t split_operand_bytes(const rms_plan_s &p, int64_t nlos, int layout)
+{
+    const int kb = layout == RMS_CHAN_MAJOR ? p.kblocks : p.kblocks_raw;
+    return (size_t)((nlos + kTileM - 1) / kTileM) * kb * (2 * kStageA);
+}
+
+cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
+                              float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
+                              cudaStream_t s)
+{
+    const bool chan = layout == RMS_CHAN_MAJOR;
+    const int mode = p.precision == RMS_BF16 ? MODE_BF16 : (p.precision == RMS_BF16X3 ? MODE_BF16X3 : MODE_FP16X3);
+    const int64_t nmt = (nlos + kTileM - 1) / kTileM;
+    if (nmt < 1) return cudaSuccess;
+    if (nmt > 0x7fffffff) return cudaErrorInvalidValue;
+
+    SplitParams sp;
+    sp.Q = Q;
+    sp.U = U;
+    sp.nlos = nlos;
+    sp.nchan = p.nchan;
+    sp.layout = layout;
+    sp.nk = chan ? p.nact : p.nchan;
+    sp.kblocks = chan ? p.kblocks : p.kblocks_raw;
+    sp.mode = mode;
+    sp.active = p.d_active;
+    sp.kbmask = p.d_kbmask;
+    sp.A = A;
+    sp.rexp = rexp;
+    sp.vec4 = !chan && (p.nchan % 4 == 0) && !(reinterpret_cast<uintptr_t>(Q) & 15) &&
+              !(reinterpret_cast<uintptr_t>(U) & 15);
+    split_kernel<<<(unsigned)nmt, 128, 0, s>>>(sp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    GemmParams P;
+    P.A = A;
+    P.nlos = nlos;
+    P.kblocks = sp.kblocks;
+    int ngroups = (P.kblocks + kGroupKBlocks - 1) / kGroupKBlocks;
+    P.group = (P.kblocks + ngroups - 1) / ngroups;
+    P.nphi = p.nphi;
+    P.ntiles_n = p.ntiles_n;
+    P.tile_n = p.tile_n;
+    P.tile_n_last = p.tile_n_last;
+    P.F = F;
+    P.pidx = pidx;
+    P.pabs = pabs;
+    P.pphi = pphi;
+    P.phi32 = p.d_phi32;
+    P.out_scale = (float)(p.K * p.wmax);
+    P.mode = mode;
+    P.rexp = mode == MODE_FP16X3 ? rexp : nullptr;
+    P.err = p.d_err;
+    P.timeout_ns = p.timeout_ns;
+    P.stages = gemm_stages(p.tile_n);
+    if (P.stages < 2) return cudaErrorInvalidConfiguration;
+    size_t smem = gemm_fixed_smem() + (size_t)P.stages * (2 * kStageA + 2 * (size_t)p.tile_n * kRowBytes) +
+                  16 * (size_t)P.stages;
+    e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = (int)(nmt < p.num_sms ? nmt : p.num_sms);
+    gemm_kernel<<<grid, kThreads, smem, s>>>(P, chan ? p.tmap_bhi : p.tmap_bhi_raw, chan ? p.tmap_blo : p.tmap_blo_raw);
+    return cudaGetLastError();
+}

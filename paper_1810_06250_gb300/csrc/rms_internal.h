@@ -92,6 +92,12 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
 cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos,
                                 int layout, int8_t *rexp, cudaStream_t s);
 
+// gemm.cu: split kernel (layout stage) + contraction kernel
+size_t split_operand_bytes(const rms_plan_s &p, int64_t nlos, int layout);
+cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
+                              float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
+                              cudaStream_t s);
+
 // api.cu: cuTensorMapEncodeTiled through the runtime's driver entry point
 bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, void *base, const cuuint64_t *dims,
                        const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr,
