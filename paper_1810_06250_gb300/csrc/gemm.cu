@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 #include <limits.h>
 
+#include <cstdlib>
 #include <cstring>
 
 #include "rms_internal.h"
@@ -43,7 +44,8 @@ constexpr int kStageA = kTileM * kRowBytes;       // 8 KB per A part
 constexpr int kTmemCols = 512;
 constexpr int kAccStride = 256;
 constexpr int kHalf = kMaxTileN / 2;              // 104 columns per epilogue thread
-constexpr int kEpiLd = 17;
+constexpr int kEpiCols = 8;                       // staging chunk: 8 columns x 32 rows per warp
+constexpr int kEpiLd = kEpiCols + 1;
 constexpr int kEpiStageBytes = kNumEpiWarps * 32 * kEpiLd * 4;
 constexpr int kSmemLimit = 227 * 1024;
 
@@ -166,7 +168,15 @@ struct GemmParams {
     int *err;
     int64_t timeout_ns;
     int32_t stages;
+    int32_t prefetch;           // L2 prefetch of the next M tile's operand
 };
+
+// One pipeline stage: the A part(s) then the B part(s); 1024-byte multiples.
+__host__ __device__ __forceinline__ uint32_t gemm_stage_bytes(int tile_n, int mode)
+{
+    const uint32_t parts = mode == MODE_BF16 ? 1u : 2u;
+    return parts * kStageA + parts * (uint32_t)tile_n * kRowBytes;
+}
 
 struct GSmem {
     uint8_t *ring;
@@ -182,7 +192,7 @@ struct GSmem {
 __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
 {
     GSmem s;
-    s.stage_bytes = 2 * kStageA + 2 * (uint32_t)P.tile_n * kRowBytes;
+    s.stage_bytes = gemm_stage_bytes(P.tile_n, P.mode);
     s.ring = base;
     s.epi = reinterpret_cast<float *>(s.ring + (size_t)P.stages * s.stage_bytes);
     s.pk_m = s.epi + kEpiStageBytes / 4;
@@ -265,8 +275,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                         const uint32_t bar = smem_u32(&S.full[s]);
                         mbar_arrive_expect_tx(bar, tx);
                         bulk_load(st, a_mt + (size_t)kb * (2 * kStageA), a_bytes, bar);
-                        tma_load_2d(st + 2 * kStageA, &tmB_hi, kb * kKBlock, nt * P.tile_n, bar);
-                        if (split) tma_load_2d(st + 2 * kStageA + b_bytes, &tmB_lo, kb * kKBlock, nt * P.tile_n, bar);
+                        tma_load_2d(st + a_bytes, &tmB_hi, kb * kKBlock, nt * P.tile_n, bar);
+                        if (split) tma_load_2d(st + a_bytes + b_bytes, &tmB_lo, kb * kKBlock, nt * P.tile_n, bar);
                         pending |= 1u << s;
                         pend_par = (pend_par & ~(1u << s)) | (ph << s);
                         if (++s == P.stages) { s = 0; ph ^= 1; }
@@ -308,7 +318,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                             tc_fence_after();
                             const uint32_t st = smem_u32(S.ring + (size_t)s * S.stage_bytes);
                             const uint32_t a_hi = st, a_lo = st + kStageA;
-                            const uint32_t b_hi = st + 2 * kStageA, b_lo = b_hi + b_bytes;
+                            const uint32_t b_hi = st + a_bytes, b_lo = b_hi + b_bytes;
 #pragma unroll
                             for (int kk = 0; kk < kKBlock / 16; ++kk) {
                                 const uint32_t ko = kk * 32;
@@ -340,7 +350,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         // A performance hint only: on a stall or an abort it stops.
         const size_t blk = (size_t)P.kblocks * (2 * kStageA);
         int mt_count = 0;
-        for (int64_t mt = blockIdx.x; mt + gridDim.x < nmt; mt += gridDim.x, ++mt_count) {
+        for (int64_t mt = blockIdx.x; P.prefetch && mt + gridDim.x < nmt; mt += gridDim.x, ++mt_count) {
             const uint64_t t0 = global_ns();
             bool go = true;
             while (go && *S.mt_started < mt_count + 1) {
@@ -415,17 +425,18 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 }
                 if (P.F != nullptr) {
 #pragma unroll
-                    for (int c0 = 0; c0 < kHalf; c0 += 16) {
+                    for (int c0 = 0; c0 < kHalf; c0 += kEpiCols) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
+                        for (int j = 0; j < kEpiCols; ++j)
                             if (c0 + j < kHalf) stg[lane * kEpiLd + j] = master[c0 + j];
                         __syncwarp();
-                        const int jj = (lane & 7) * 2;
-                        const int kk = kbase + (c0 >> 1) + (lane & 7);
+                        // 4 lanes per row (one complex each), 8 rows per store instruction
+                        const int jj = (lane & 3) * 2;
+                        const int kk = kbase + (c0 >> 1) + (lane & 3);
                         const bool colok = c0 + jj < min(ncols, kHalf) && kk < P.nphi;
 #pragma unroll
-                        for (int it = 0; it < 8; ++it) {
-                            const int r = 4 * it + (lane >> 3);
+                        for (int it = 0; it < 4; ++it) {
+                            const int r = 8 * it + (lane >> 2);
                             const int64_t grow = mt * kTileM + 32 * q + r;
                             if (colok && grow < P.nlos) {
                                 const float2 val = make_float2(stg[r * kEpiLd + jj], stg[r * kEpiLd + jj + 1]);
@@ -478,9 +489,9 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
 
 size_t gemm_fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 8 + 8 * 32 + 32; }
 
-int gemm_stages(int tile_n)
+int gemm_stages(int tile_n, int mode)
 {
-    size_t st = 2 * (size_t)kStageA + 2 * (size_t)tile_n * kRowBytes;
+    size_t st = gemm_stage_bytes(tile_n, mode);
     int s = (int)((kSmemLimit - gemm_fixed_smem()) / (st + 16));
     return s > 8 ? 8 : s;
 }
@@ -542,13 +553,24 @@ cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *
     P.rexp = mode == MODE_FP16X3 ? rexp : nullptr;
     P.err = p.d_err;
     P.timeout_ns = p.timeout_ns;
-    P.stages = gemm_stages(p.tile_n);
+    P.stages = gemm_stages(p.tile_n, mode);
+    // RMS_L2_PREFETCH=1 turns on the L2 prefetch of the next M tile's operand (off by
+    // default: on the LOFAR cube it evicted the current M tile's operand and cost 6%)
+    static const int prefetch = [] {
+        const char *v = std::getenv("RMS_L2_PREFETCH");
+        return (v && v[0] == '1') ? 1 : 0;
+    }();
+    P.prefetch = prefetch;
     if (P.stages < 2) return cudaErrorInvalidConfiguration;
-    size_t smem = gemm_fixed_smem() + (size_t)P.stages * (2 * kStageA + 2 * (size_t)p.tile_n * kRowBytes) +
-                  16 * (size_t)P.stages;
+    size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(p.tile_n, mode) + 16 * (size_t)P.stages;
     e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int grid = (int)(nmt < p.num_sms ? nmt : p.num_sms);
+    int ctas = p.num_sms;
+    if (const char *v = std::getenv("RMS_GEMM_CTAS")) {   // tuning knob: persistent CTAs
+        int c = std::atoi(v);
+        if (c >= 1 && c <= p.num_sms) ctas = c;
+    }
+    int grid = (int)(nmt < ctas ? nmt : ctas);
     gemm_kernel<<<grid, kThreads, smem, s>>>(P, chan ? p.tmap_bhi : p.tmap_bhi_raw, chan ? p.tmap_blo : p.tmap_blo_raw);
     return cudaGetLastError();
 }
