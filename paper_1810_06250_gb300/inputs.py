@@ -101,9 +101,10 @@ CONFIGS = {
     # MWA-like large phases: 1024^2 LOS, 1536 channels 72-231 MHz, 4001 phi in +-2000
     "mwa": CubeConfig("mwa", 1024 * 1024, 1536, 72e6, 231e6, 4001, -2000.0, 2000.0, seed=1004,
                       phi0=(-1800.0, 1800.0)),
-    # learned-proposal workload: 2048^2 LOS on the LOFAR band and grid, SNR 5-100
+    # learned-proposal workload: 2048^2 LOS on the LOFAR band and grid, SNR 5-100,
+    # thin components and Burn slabs mixed as on the LOFAR cube
     "learned": CubeConfig("learned", 2048 * 2048, 400, 115e6, 178e6, 401, -100.0, 100.0, seed=1005,
-                          flag_frac=0.10, slab_prob=1.0, slab_w=10.0, snr=(5.0, 100.0)),
+                          flag_frac=0.10, slab_prob=0.5, slab_w=10.0, snr=(5.0, 100.0)),
 }
 
 
