@@ -216,6 +216,166 @@ const char *rms_status_string(rms_status s);
  * RMS_ERR_TIMEOUT on the plan and returns. */
 rms_status rms_plan_set_timeout(rms_plan_t plan, int64_t ns);
 
+/* ==========================================================================
+ * Synthetic sources on the device (Sec. 2.1 source models)
+ * ========================================================================== */
+
+/*
+ * Source model of rms_generate.  Per line of sight: a component count uniform
+ * in [ncomp_min, ncomp_max] (1 <= min <= max <= 3); per component phi0 ~
+ * U(phi0_min, phi0_max), p0 ~ U(p0_min, p0_max), chi0 ~ U(0, pi); with
+ * probability slab_prob the component is a Burn slab of width W ~ U(0, slab_w)
+ * centred on phi0, else Faraday thin:
+ *     P(lambda^2) = p0 exp(2i (chi0 + phi0 lambda^2)) [sin(W lambda^2) / (W lambda^2)]
+ * (Eqs. PAdefn, Pdefn; the slab factor integrates Eq. Predefn over the slab).
+ * Gaussian noise of standard deviation sigma is added to Q and to U; when
+ * snr_min > 0, sigma is instead drawn per LOS so that max p0 / sigma_F ~
+ * U(snr_min, snr_max), sigma_F = sigma sqrt(sum w^2) / sum w (the noise of F).
+ * All draws are counter based on (seed, LOS index, draw number) -- see
+ * csrc/generate.cu for the exact definition -- so one LOS can be regenerated
+ * alone.
+ */
+typedef struct {
+    uint64_t seed;
+    int32_t ncomp_min, ncomp_max;
+    double phi0_min, phi0_max;   /* rad m^-2 */
+    double p0_min, p0_max;
+    double slab_prob, slab_w;    /* slab_w in rad m^-2 */
+    double sigma;                /* used when snr_min <= 0 */
+    double snr_min, snr_max;
+} rms_source_model;
+
+/*
+ * Write Q and U (device, nchan * nlos floats each, in `layout`) for lines of
+ * sight los0 .. los0 + nlos - 1 of the source model, on the plan's channels
+ * (lambda^2 and weights of the plan).  Asynchronous on `stream`.  Returns
+ * RMS_ERR_INVALID_ARG for a NULL pointer, nlos < 0, los0 < 0 or a model outside
+ * the ranges above.
+ */
+rms_status rms_generate(rms_plan_t plan, const rms_source_model *model, int64_t los0, int64_t nlos,
+                        int32_t layout, float *Q, float *U, void *stream);
+
+/* ==========================================================================
+ * Learned peak proposal (not in the paper)
+ *
+ * A small network looks at one LOS's Q/U spectrum and proposes the bin of the
+ * full phi grid that holds max |F|; exact synthesis (Eq. Fsum) then runs only
+ * on a narrow window of a twice finer grid around the proposal, and the LOS
+ * falls back to the full grid when the proposal is not confident or the
+ * window's maximum lands on its edge.  Everything here runs on the plan's
+ * device in the library's own kernels.
+ *
+ * Network: input x = [Q_a0, U_a0, Q_a1, U_a1, ...] / s over the plan's active
+ * channels, s = RMS of |P| over them (1 for an all-zero spectrum);
+ * h = relu(W1 x + b1) (W1: [hidden][2 nact]); logits z = W2 h + b2
+ * (W2: [nbins][hidden], nbins = the plan's nphi).  BF16 weights and
+ * activations, FP32 accumulation, FP32 master weights and AdamW moments.
+ * Parameters are one flat FP32 array: W1 (row-major), b1, W2 (row-major), b2.
+ * ========================================================================== */
+
+typedef struct rms_net_s *rms_net_t;
+typedef struct rms_window_s *rms_window_t;
+
+/*
+ * Create a network for `plan` (a tensor-core plan: RMS_BF16, RMS_BF16X3 or
+ * RMS_FP16X3 -- else RMS_ERR_UNSUPPORTED -- with nphi <= 512).  hidden: 16 ..
+ * 256, a multiple of 16.  max_batch: 1 .. 65536, the largest nlos of
+ * rms_net_grad / rms_train_step (their scratch is allocated here).  Weights are
+ * drawn from seed (uniform, fan-in scaled), biases 0.  The network refers to
+ * the plan, which must outlive it.  Synchronous.
+ */
+rms_status rms_net_create(rms_net_t *net, rms_plan_t plan, int32_t hidden, int32_t max_batch, uint64_t seed);
+
+/* Destroy a network (synchronises its device); NULL is accepted. */
+rms_status rms_net_destroy(rms_net_t net);
+
+enum { RMS_NET_NPARAMS = 0, RMS_NET_NIN = 1, RMS_NET_HIDDEN = 2, RMS_NET_NBINS = 3, RMS_NET_MAX_BATCH = 4,
+       RMS_NET_STEPS = 5 };
+rms_status rms_net_info(rms_net_t net, int32_t what, int64_t *value);
+
+/*
+ * Copy the flat FP32 parameters (RMS_NET_PARAMS) or the last gradients
+ * (RMS_NET_GRADS) to `host` (set = 0), or load parameters from `host`
+ * (set = 1, RMS_NET_PARAMS only; also resets the AdamW moments and step).
+ * count must equal RMS_NET_NPARAMS.  Synchronous.
+ */
+enum { RMS_NET_PARAMS = 0, RMS_NET_GRADS = 1 };
+rms_status rms_net_params(rms_net_t net, int32_t which, float *host, int64_t count, int32_t set);
+
+/*
+ * Run the network on a cube (arguments as rms_synth).  Outputs (device, any may
+ * be NULL): logits [nlos][nbins] floats; bin [nlos] int32, argmax of the
+ * logits (lowest on ties); conf [nlos] float, the softmax mass of the bins
+ * within conf_halfwidth of bin (conf_halfwidth < 0: the largest probability).
+ * Takes per-call scratch from the stream-ordered pool (2 bytes per (LOS,
+ * contraction channel) plus 2 * hidden bytes per LOS).  Asynchronous.
+ */
+rms_status rms_propose(rms_net_t net, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                       int32_t conf_halfwidth, float *logits, int32_t *bin, float *conf, void *stream);
+
+/*
+ * Mean cross-entropy of the network on a batch with labels `label` (device
+ * [nlos] int32 in 0 .. nbins - 1), and its gradient w.r.t. every parameter,
+ * kept in the network (read with rms_net_params(RMS_NET_GRADS)).  1 <= nlos <=
+ * max_batch.  loss: device float, or NULL.  Asynchronous.  Labels out of range
+ * give undefined gradients (they are not checked on the device).
+ */
+rms_status rms_net_grad(rms_net_t net, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                        const int32_t *label, float *loss, void *stream);
+
+/*
+ * One training step: rms_net_grad, then AdamW on the FP32 master weights
+ * (decoupled weight decay on W1 and W2 only, bias-corrected moments) and a
+ * refresh of the BF16 weight copies.  Asynchronous.
+ */
+rms_status rms_train_step(rms_net_t net, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                          const int32_t *label, float lr, float beta1, float beta2, float eps, float weight_decay,
+                          float *loss, void *stream);
+
+/*
+ * A window of `width` points (8 .. 128, a multiple of 8) on the fine grid
+ * phi_0 + n D / 2 of a plan whose phi grid is uniform with step D (n = 0 ..
+ * 2 (nphi - 1)).  The plan must be RMS_BF16 or RMS_BF16X3 (else
+ * RMS_ERR_UNSUPPORTED) with a uniform grid (else RMS_ERR_INVALID_ARG).  Builds
+ * the rotation table T[n][j] = exp(-2i phi_n (lambda_j^2 - lambda_0^2)) (argument
+ * reduced in FP64) and the window's phase matrix for the offsets m D / 2,
+ * m = -width/2 .. width/2 - 1, so that for every LOS
+ *     F(phi_n + m D / 2) = K sum_j w_j (P_j T[n][j]) exp(-2i (m D / 2)(lambda_j^2 - lambda_0^2)),
+ * an exact identity of Eq. Fsum.  Synchronous.  The plan must outlive it.
+ */
+rms_status rms_window_create(rms_window_t *win, rms_plan_t plan, int32_t width);
+rms_status rms_window_destroy(rms_window_t win);
+
+/*
+ * Exact synthesis on one window per LOS.  centre: device [nlos] int32, the
+ * fine-grid index n of each window's centre, width/2 <= n <= 2 (nphi - 1) -
+ * width/2 + 1 (checked on the device: an out-of-range centre is clamped).  The
+ * window covers fine points n - width/2 .. n + width/2 - 1.  Outputs (device,
+ * any may be NULL): F_out [nlos][width] complex64; widx [nlos] int32, index in
+ * the window of max |F| (lowest on ties, -1 if none finite); wabs [nlos] float,
+ * |F| there; wphi [nlos] float, phi there.  Other arguments as rms_synth.
+ * Asynchronous; per-call scratch as rms_synth.
+ */
+rms_status rms_synth_window(rms_window_t win, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                            const int32_t *centre, float *F_out, int32_t *widx, float *wabs, float *wphi,
+                            void *stream);
+
+/*
+ * The learned peak map: rms_propose (confidence = softmax mass within
+ * width/4 - 2 bins of the proposal), a window centred on fine point 2 bin
+ * (clamped into the grid), and a full-grid fallback for every LOS whose
+ * confidence is below tau or NaN, whose window maximum is the window's first
+ * or last point, or whose window holds no finite |F|.  Outputs (device, any
+ * may be NULL): phi_peak, peak_abs [nlos] floats (as rms_synth; from the
+ * window or the full grid); fallback [nlos] int32, 1 where the full grid was
+ * used; nfallback: device int64, the number of fallbacks.  net and win must
+ * belong to the same plan.  Asynchronous; per-call scratch as rms_synth plus
+ * 20 bytes per LOS.
+ */
+rms_status rms_peakmap_learned(rms_window_t win, rms_net_t net, const float *Q, const float *U, int64_t nlos,
+                               int32_t layout, float tau, float *phi_peak, float *peak_abs, int32_t *fallback,
+                               int64_t *nfallback, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,10 @@ from ._binding import (  # noqa: F401
     RMS_INFO_TILE_N, RMS_LOS_MAJOR, RMS_OK,
     RMS_NOALLOC_MAX_LOS, load, rms_plan_create, rms_plan_destroy, rms_plan_get, rms_plan_info, rms_plan_set_timeout,
     rms_plan_sync, rms_rmsf, rms_status_string, rms_synth, rms_synth_host, rms_synth_noalloc,
+    RMS_NET_GRADS, RMS_NET_HIDDEN, RMS_NET_MAX_BATCH, RMS_NET_NBINS, RMS_NET_NIN, RMS_NET_NPARAMS, RMS_NET_PARAMS,
+    RMS_NET_STEPS, rms_source_model, rms_generate, rms_net_create, rms_net_destroy, rms_net_info, rms_net_params,
+    rms_propose, rms_net_grad, rms_train_step, rms_window_create, rms_window_destroy, rms_synth_window,
+    rms_peakmap_learned,
 )
 
 

@@ -32,7 +32,19 @@ LAYOUTS = {"chan": RMS_CHAN_MAJOR, "los": RMS_LOS_MAJOR}
 # Every symbol include/rms.h declares (checked by the ABI test).
 EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_synth_noalloc",
            "rms_plan_sync", "rms_plan_info", "rms_plan_get", "rms_plan_destroy", "rms_status_string",
-           "rms_plan_set_timeout")
+           "rms_plan_set_timeout", "rms_generate", "rms_net_create", "rms_net_destroy", "rms_net_info",
+           "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
+           "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned")
+(RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
+RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
+
+
+class rms_source_model(ctypes.Structure):
+    """Mirror of the C struct rms_source_model (include/rms.h)."""
+    _fields_ = [("seed", ctypes.c_uint64), ("ncomp_min", ctypes.c_int32), ("ncomp_max", ctypes.c_int32),
+                ("phi0_min", ctypes.c_double), ("phi0_max", ctypes.c_double), ("p0_min", ctypes.c_double),
+                ("p0_max", ctypes.c_double), ("slab_prob", ctypes.c_double), ("slab_w", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("snr_min", ctypes.c_double), ("snr_max", ctypes.c_double)]
 RMS_NOALLOC_MAX_LOS = 1 << 22
 
 
@@ -69,6 +81,19 @@ def load(path: str = LIB_PATH):
             "rms_plan_get": [P, _i32, P, _i64],
             "rms_plan_destroy": [P],
             "rms_plan_set_timeout": [P, _i64],
+            "rms_generate": [P, P, _i64, _i64, _i32, P, P, P],
+            "rms_net_create": [ctypes.POINTER(P), P, _i32, _i32, ctypes.c_uint64],
+            "rms_net_destroy": [P],
+            "rms_net_info": [P, _i32, P],
+            "rms_net_params": [P, _i32, P, _i64, _i32],
+            "rms_propose": [P, P, P, _i64, _i32, _i32, P, P, P, P],
+            "rms_net_grad": [P, P, P, _i64, _i32, P, P, P],
+            "rms_train_step": [P, P, P, _i64, _i32, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, P, P],
+            "rms_window_create": [ctypes.POINTER(P), P, _i32],
+            "rms_window_destroy": [P],
+            "rms_synth_window": [P, P, P, _i64, _i32, P, P, P, P, P, P],
+            "rms_peakmap_learned": [P, P, P, P, _i64, _i32, ctypes.c_float, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -233,3 +258,91 @@ def rms_plan_get(plan: int, what: int) -> np.ndarray:
     out = np.empty(shape, dtype=dt)
     _check(load().rms_plan_get(plan, int(what), out.ctypes.data, out.nbytes), "rms_plan_get")
     return out
+
+
+def rms_generate(plan: int, model: rms_source_model, los0: int, nlos: int, layout, Q, U, stream=None):
+    """Seeded synthetic Q/U on the device (include/rms.h); Q, U CUDA float32 tensors."""
+    import torch
+    st = load().rms_generate(plan, ctypes.byref(model), int(los0), int(nlos), _layout(layout),
+                             _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), _stream(stream))
+    _check(st, "rms_generate")
+
+
+def rms_net_create(plan: int, hidden: int, max_batch: int, seed: int) -> int:
+    out = _c_void_p()
+    _check(load().rms_net_create(ctypes.byref(out), plan, int(hidden), int(max_batch), int(seed)), "rms_net_create")
+    return out.value
+
+
+def rms_net_destroy(net: int):
+    _check(load().rms_net_destroy(net), "rms_net_destroy")
+
+
+def rms_net_info(net: int, what: int) -> int:
+    v = _i64()
+    _check(load().rms_net_info(net, int(what), ctypes.byref(v)), "rms_net_info")
+    return v.value
+
+
+def rms_net_params(net: int, which: int, host: np.ndarray, set: bool = False):
+    """Copy parameters/gradients to (set=False) or parameters from (set=True) a float32 numpy array."""
+    _check(load().rms_net_params(net, int(which), _hptr(host, "float32", "host"), host.size, 1 if set else 0),
+           "rms_net_params")
+
+
+def rms_propose(net: int, Q, U, nlos: int, layout, conf_halfwidth: int = -1, logits=None, bin=None, conf=None,
+                stream=None):
+    import torch
+    st = load().rms_propose(net, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                            _layout(layout), int(conf_halfwidth), _dptr(logits, torch.float32, "logits"),
+                            _dptr(bin, torch.int32, "bin"), _dptr(conf, torch.float32, "conf"), _stream(stream))
+    _check(st, "rms_propose")
+
+
+def rms_net_grad(net: int, Q, U, nlos: int, layout, label, loss=None, stream=None):
+    import torch
+    st = load().rms_net_grad(net, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                             _layout(layout), _dptr(label, torch.int32, "label"), _dptr(loss, torch.float32, "loss"),
+                             _stream(stream))
+    _check(st, "rms_net_grad")
+
+
+def rms_train_step(net: int, Q, U, nlos: int, layout, label, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                   eps: float = 1e-8, weight_decay: float = 0.0, loss=None, stream=None):
+    import torch
+    st = load().rms_train_step(net, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                               _layout(layout), _dptr(label, torch.int32, "label"), float(lr), float(beta1),
+                               float(beta2), float(eps), float(weight_decay), _dptr(loss, torch.float32, "loss"),
+                               _stream(stream))
+    _check(st, "rms_train_step")
+
+
+def rms_window_create(plan: int, width: int) -> int:
+    out = _c_void_p()
+    _check(load().rms_window_create(ctypes.byref(out), plan, int(width)), "rms_window_create")
+    return out.value
+
+
+def rms_window_destroy(win: int):
+    _check(load().rms_window_destroy(win), "rms_window_destroy")
+
+
+def rms_synth_window(win: int, Q, U, nlos: int, layout, centre, F_out=None, widx=None, wabs=None, wphi=None,
+                     stream=None):
+    import torch
+    st = load().rms_synth_window(win, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                                 _layout(layout), _dptr(centre, torch.int32, "centre"), _dptr(F_out, None, "F_out"),
+                                 _dptr(widx, torch.int32, "widx"), _dptr(wabs, torch.float32, "wabs"),
+                                 _dptr(wphi, torch.float32, "wphi"), _stream(stream))
+    _check(st, "rms_synth_window")
+
+
+def rms_peakmap_learned(win: int, net: int, Q, U, nlos: int, layout, tau: float, phi_peak=None, peak_abs=None,
+                        fallback=None, nfallback=None, stream=None):
+    import torch
+    st = load().rms_peakmap_learned(win, net, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"),
+                                    int(nlos), _layout(layout), float(tau), _dptr(phi_peak, torch.float32, "phi_peak"),
+                                    _dptr(peak_abs, torch.float32, "peak_abs"),
+                                    _dptr(fallback, torch.int32, "fallback"),
+                                    _dptr(nfallback, torch.int64, "nfallback"), _stream(stream))
+    _check(st, "rms_peakmap_learned")

@@ -61,6 +61,7 @@ void free_plan(rms_plan_s *p)
     cudaFree(p->d_blo);
     cudaFree(p->d_R64);
     cudaFree(p->d_dl2_all);
+    cudaFree(p->d_lambda2_all);
     cudaFree(p->d_w_all);
     if (p->d_bhi_raw != p->d_bhi) cudaFree(p->d_bhi_raw);
     if (p->d_blo_raw != p->d_blo) cudaFree(p->d_blo_raw);
@@ -170,9 +171,11 @@ const char *rms_status_string(rms_status s)
     return "unknown status";
 }
 
-rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, int32_t axis_kind,
-                           const double *weights, const double *phi, int32_t nphi, int32_t precision,
-                           int32_t device)
+}  // extern "C"
+
+rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nchan, int32_t axis_kind,
+                                const double *weights, const double *phi, int32_t nphi, int32_t precision,
+                                int32_t device, int32_t max_tile_cap)
 {
     if (!out) return RMS_ERR_INVALID_ARG;
     *out = nullptr;
@@ -263,6 +266,8 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
     RMS_TRY(dalloc(&p->d_l2x32, p->nact));
     RMS_TRY(dalloc(&p->d_w32, p->nact));
     RMS_TRY(dalloc(&p->d_R64, 2 * (size_t)nphi));
+    RMS_TRY(dalloc(&p->d_lambda2_all, nchan));
+    RMS_TRY(cudaMemcpy(p->d_lambda2_all, lam2.data(), nchan * sizeof(double), cudaMemcpyHostToDevice));
     RMS_TRY(cudaMemcpy(p->d_active, p->active.data(), p->nact * sizeof(int32_t), cudaMemcpyHostToDevice));
     RMS_TRY(cudaMemcpy(p->d_dl2, dl2.data(), p->nact * sizeof(double), cudaMemcpyHostToDevice));
     RMS_TRY(cudaMemcpy(p->d_wact, wact.data(), p->nact * sizeof(double), cudaMemcpyHostToDevice));
@@ -279,10 +284,10 @@ rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, i
         // RMS_MAX_TILE_N (16..208, multiple of 16) in the environment lowers the phase
         // rows per tensor-core tile (a tuning knob: smaller tiles leave shared memory
         // for more pipeline stages)
-        int max_tile = kMaxTileN;
+        int max_tile = max_tile_cap;
         if (const char *v = std::getenv("RMS_MAX_TILE_N")) {
             int t = std::atoi(v);
-            if (t >= 16 && t <= kMaxTileN && t % 16 == 0) max_tile = t;
+            if (t >= 16 && t <= max_tile_cap && t % 16 == 0) max_tile = t;
         }
         p->ntiles_n = (N + max_tile - 1) / max_tile;
         int per = (N + p->ntiles_n - 1) / p->ntiles_n;
@@ -351,6 +356,15 @@ fail:
     cudaGetLastError();
     free_plan(p);
     return from_cuda(e);
+}
+
+extern "C" {
+
+rms_status rms_plan_create(rms_plan_t *out, const double *axis, int32_t nchan, int32_t axis_kind,
+                           const double *weights, const double *phi, int32_t nphi, int32_t precision,
+                           int32_t device)
+{
+    return plan_create_internal(out, axis, nchan, axis_kind, weights, phi, nphi, precision, device, kMaxTileN);
 }
 
 rms_status rms_plan_destroy(rms_plan_t p)

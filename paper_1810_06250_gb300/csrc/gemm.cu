@@ -44,6 +44,7 @@ constexpr int kStageA = kTileM * kRowBytes;       // 8 KB per A part
 constexpr int kTmemCols = 512;
 constexpr int kAccStride = 256;
 constexpr int kHalf = kMaxTileN / 2;              // 104 columns per epilogue thread
+constexpr int kHalfRot = 64;                      // rotating (window) kernel: tile_n <= 128
 constexpr int kEpiCols = 8;                       // staging chunk: 8 columns x 32 rows per warp
 constexpr int kEpiLd = kEpiCols + 1;
 constexpr int kEpiStageBytes = kNumEpiWarps * 32 * kEpiLd * 4;
@@ -56,16 +57,22 @@ enum { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_FP16X3 = 2 };
 // ----------------------------------------------------------------------------
 struct SplitParams {
     const float *Q, *U;
-    int64_t nlos;
+    int64_t nlos_src;           // lines of sight in the cube (channel-major row stride)
+    int64_t nout;               // output rows (the grid covers them)
+    const int64_t *rows;        // optional: output row r reads cube row rows[r]
+    const int64_t *count;       // optional device count: rows >= *count are left as padding
     int32_t nchan, layout, nk, kblocks, mode;
     int32_t vec4;               // LOS-major rows are 16-byte aligned: vector loads
     const int32_t *active;      // channel-major: active channel list
     const uint16_t *kbmask;     // LOS-major: per K block, bit i = channel 16 kb + i active
     uint8_t *A;                 // [nmt][kblocks][16 KB]
-    int8_t *rexp;               // [nlos] (FP16X3)
+    int8_t *rexp;               // [nout] (FP16X3)
+    float *rscale;              // optional [nout]: 1 / RMS of |P| over the nact_norm active channels
+    int32_t nact_norm;
 };
 
-__device__ __forceinline__ void load_kblock(const SplitParams &P, int64_t row, int kb, float (&q)[16], float (&u)[16])
+__device__ __forceinline__ void load_kblock(const SplitParams &P, int64_t src, bool valid, int kb, float (&q)[16],
+                                            float (&u)[16])
 {
     const int c0 = kb * kChanPerKBlock;
     if (P.layout == RMS_CHAN_MAJOR) {
@@ -73,18 +80,18 @@ __device__ __forceinline__ void load_kblock(const SplitParams &P, int64_t row, i
         for (int i = 0; i < 16; ++i) {
             q[i] = 0.f;
             u[i] = 0.f;
-            if (c0 + i < P.nk && row < P.nlos) {
-                const int64_t off = (int64_t)__ldg(P.active + c0 + i) * P.nlos + row;
+            if (c0 + i < P.nk && valid) {
+                const int64_t off = (int64_t)__ldg(P.active + c0 + i) * P.nlos_src + src;
                 q[i] = __ldg(P.Q + off);
                 u[i] = __ldg(P.U + off);
             }
         }
     } else {
         const uint32_t live = __ldg(P.kbmask + kb);
-        if (P.vec4 && row < P.nlos && c0 + 16 <= P.nchan) {
+        if (P.vec4 && valid && c0 + 16 <= P.nchan) {
             // 16 contiguous channels of this row: four 16-byte loads per array
-            const float4 *q4 = reinterpret_cast<const float4 *>(P.Q + row * P.nchan + c0);
-            const float4 *u4 = reinterpret_cast<const float4 *>(P.U + row * P.nchan + c0);
+            const float4 *q4 = reinterpret_cast<const float4 *>(P.Q + src * P.nchan + c0);
+            const float4 *u4 = reinterpret_cast<const float4 *>(P.U + src * P.nchan + c0);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const float4 a = __ldg(q4 + v), b = __ldg(u4 + v);
@@ -99,9 +106,9 @@ __device__ __forceinline__ void load_kblock(const SplitParams &P, int64_t row, i
             for (int i = 0; i < 16; ++i) {
                 q[i] = 0.f;
                 u[i] = 0.f;
-                if (((live >> i) & 1u) && row < P.nlos) {
-                    q[i] = __ldg(P.Q + row * P.nchan + c0 + i);
-                    u[i] = __ldg(P.U + row * P.nchan + c0 + i);
+                if (((live >> i) & 1u) && valid) {
+                    q[i] = __ldg(P.Q + src * P.nchan + c0 + i);
+                    u[i] = __ldg(P.U + src * P.nchan + c0 + i);
                 }
             }
         }
@@ -113,13 +120,18 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
     const int m = threadIdx.x;
     const int64_t mt = blockIdx.x;
     const int64_t row = mt * kTileM + m;
+    const int64_t n_eff = P.count ? min(*P.count, P.nout) : P.nout;
+    if (mt * kTileM >= n_eff) return;          // tiles past a device-side count stay untouched
+    const bool valid = row < n_eff;
+    const int64_t src = valid ? (P.rows ? P.rows[row] : row) : 0;
     const int sw = (m >> 1) & 3;
     float scale = 1.0f;
     if (P.mode == MODE_FP16X3) {
+        // the row's largest |value| sets its power-of-two scale: a first pass
         float mx = 0.f;
         for (int kb = 0; kb < P.kblocks; ++kb) {
             float q[16], u[16];
-            load_kblock(P, row, kb, q, u);
+            load_kblock(P, src, valid, kb, q, u);
 #pragma unroll
             for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fmaxf(fabsf(q[i]), fabsf(u[i])));
         }
@@ -127,12 +139,17 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
         if (mx > 0.f && isfinite(mx)) { frexpf(mx, &e); e = 15 - e; }
         e = max(-100, min(100, e));
         scale = ldexpf(1.0f, e);
-        if (row < P.nlos) P.rexp[row] = (int8_t)e;
+        if (valid) P.rexp[row] = (int8_t)e;
     }
+    float ss = 0.f;
     uint8_t *dst = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
     for (int kb = 0; kb < P.kblocks; ++kb, dst += 2 * kStageA) {
         float q[16], u[16];
-        load_kblock(P, row, kb, q, u);
+        load_kblock(P, src, valid, kb, q, u);
+        if (P.rscale) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) ss = fmaf(q[i], q[i], fmaf(u[i], u[i], ss));
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             uint32_t hi[4], lo[4];
@@ -148,6 +165,37 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
                 *reinterpret_cast<uint4 *>(dst + kStageA + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
     }
+    if (P.rscale && valid) {
+        const float rms = sqrtf(ss / (float)P.nact_norm);
+        P.rscale[row] = rms > 0.f ? 1.0f / rms : 1.0f;
+    }
+}
+
+// Copy whole operand rows between split images: output row j <- image row
+// rows[j], re-swizzled for its new position; rows at or past *count are not
+// written.  One thread per (row, K block).
+__global__ void __launch_bounds__(128) image_gather_kernel(const uint8_t *src, uint8_t *dst, int32_t kblocks,
+                                                           const int64_t *rows, const int64_t *count,
+                                                           int64_t nmax, int32_t parts)
+{
+    const int m = threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.x * kTileM + m;
+    const int64_t n = min(*count, nmax);
+    if ((int64_t)blockIdx.x * kTileM >= n) return;
+    if (j >= n) return;
+    const int64_t r = rows[j];
+    const int ms = (int)(r % kTileM), swd = (m >> 1) & 3, sws = (ms >> 1) & 3;
+    const uint8_t *sb = src + (size_t)(r / kTileM) * kblocks * (2 * kStageA);
+    uint8_t *db = dst + (size_t)blockIdx.x * kblocks * (2 * kStageA);
+    for (int kb = 0; kb < kblocks; ++kb)
+        for (int part = 0; part < parts; ++part) {
+            const size_t base = (size_t)kb * (2 * kStageA) + (size_t)part * kStageA;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(sb + base + ms * kRowBytes + ((c ^ sws) << 4));
+                *reinterpret_cast<uint4 *>(db + base + m * kRowBytes + ((c ^ swd) << 4)) = v;
+            }
+        }
 }
 
 // ----------------------------------------------------------------------------
@@ -155,7 +203,9 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
 // ----------------------------------------------------------------------------
 struct GemmParams {
     const uint8_t *A;           // split operand, [nmt][kblocks][16 KB]
-    int64_t nlos;
+    int64_t nlos;               // operand rows
+    const int64_t *count;       // optional device count (<= nlos) of live rows
+    const int64_t *rows;        // optional: results of row r go to output row rows[r]
     int32_t kblocks, group;
     int32_t nphi, ntiles_n, tile_n, tile_n_last;
     float *F;
@@ -169,6 +219,11 @@ struct GemmParams {
     int64_t timeout_ns;
     int32_t stages;
     int32_t prefetch;           // L2 prefetch of the next M tile's operand
+    // window rotation (rotating kernel only): row r's operand is multiplied by
+    // T[clamp(centre[r], cmin, cmax)][channel] before it enters the MMA
+    const int32_t *centre;
+    const float2 *T;
+    int32_t ldT, cmin, cmax;
 };
 
 // One pipeline stage: the A part(s) then the B part(s); 1024-byte multiples.
@@ -183,7 +238,7 @@ struct GSmem {
     uint32_t stage_bytes;
     float *epi, *pk_m;
     int *pk_i;
-    uint64_t *full, *empty, *tfull, *tempty, *pkfull, *pkempty, *mma_done;
+    uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;
     uint32_t *tmem_slot;
     volatile int *abort_flag;
     volatile int *mt_started;   // M tiles the producer has started (read by the L2 prefetcher)
@@ -200,7 +255,8 @@ __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
     uint64_t *b = reinterpret_cast<uint64_t *>(s.pk_i + 2 * 4 * 32);
     s.full = b;
     s.empty = s.full + P.stages;
-    s.tfull = s.empty + P.stages;
+    s.conv = s.empty + P.stages;
+    s.tfull = s.conv + P.stages;
     s.tempty = s.tfull + 2;
     s.pkfull = s.tempty + 2;
     s.pkempty = s.pkfull + 8;
@@ -211,7 +267,13 @@ __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
     return s;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+constexpr int kConvWarp0 = 12;   // rotating kernel: warps 12-15 rotate the A operand in place
+
+// HALF: columns of the tile per epilogue thread (tile_n <= 2 HALF).  ROT: the
+// window variant, 512 threads, whose converter warps rotate each stage's A
+// rows in shared memory before the MMA reads them.
+template <int HALF, bool ROT>
+__global__ void __launch_bounds__(ROT ? 512 : kThreads, 1)
 gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtensorMap tmB_hi,
             const __grid_constant__ CUtensorMap tmB_lo)
 {
@@ -219,7 +281,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const GSmem S = gcarve(base, P);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nmt = (P.nlos + kTileM - 1) / kTileM;
+    const int64_t nlos = P.count ? min(*P.count, P.nlos) : P.nlos;
+    const int64_t nmt = (nlos + kTileM - 1) / kTileM;
     const bool split = P.mode != MODE_BF16;
     const int ngroups = (P.kblocks + P.group - 1) / P.group;
     const uint32_t a_bytes = split ? 2 * kStageA : kStageA;
@@ -229,6 +292,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         for (int s = 0; s < P.stages; ++s) {
             mbar_init(smem_u32(&S.full[s]), 1);
             mbar_init(smem_u32(&S.empty[s]), 1);
+            mbar_init(smem_u32(&S.conv[s]), 4);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.tfull[b]), 1);
@@ -311,7 +375,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                         const uint32_t d = tmem_base + (uint32_t)(b * kAccStride);
                         const int kb0 = g * P.group, kb1 = min(P.kblocks, kb0 + P.group);
                         for (int kb = kb0; kb < kb1; ++kb) {
-                            if (!wait_bounded(smem_u32(&S.full[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
+                            const uint64_t *ready = ROT ? &S.conv[s] : &S.full[s];
+                            if (!wait_bounded(smem_u32(ready), ph, S.abort_flag, P.err, P.timeout_ns)) {
                                 ok = false;
                                 break;
                             }
@@ -362,7 +427,60 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             for (size_t off = (size_t)lane * 4096; off < blk; off += 32 * 4096)
                 prefetch_l2(nxt + off, (uint32_t)min((size_t)4096, blk - off));
         }
-    } else if (warp >= kEpiWarp0) {
+    } else if (ROT && warp >= kConvWarp0) {
+        // ------------------------------------------------------------ rotation
+        // Thread r owns operand row r: P' = (hi + lo) T[centre][channel] in FP32,
+        // split again and written back in place, before the MMA may read it.
+        const int r = threadIdx.x - 32 * kConvWarp0;
+        const int sw = (r >> 1) & 3;
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x) {
+            const int64_t row = mt * kTileM + r;
+            const bool live = row < nlos;
+            int c = P.cmin;
+            if (live) c = max(P.cmin, min(P.cmax, P.centre[row]));
+            const float4 *trow = reinterpret_cast<const float4 *>(P.T + (size_t)c * P.ldT);
+            for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
+                for (int kb = 0; kb < P.kblocks; ++kb) {
+                    float4 t[8];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) t[v] = live ? __ldg(trow + kb * 8 + v) : make_float4(1.f, 0.f, 1.f, 0.f);
+                    if (!warp_wait(smem_u32(&S.full[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    if (live) {
+                        uint8_t *st = S.ring + (size_t)s * S.stage_bytes;
+#pragma unroll
+                        for (int ch = 0; ch < 4; ++ch) {
+                            const uint32_t off = (uint32_t)r * kRowBytes + ((uint32_t)(ch ^ sw) << 4);
+                            uint4 hv = *reinterpret_cast<const uint4 *>(st + off);
+                            uint4 lv = split ? *reinterpret_cast<const uint4 *>(st + kStageA + off) : make_uint4(0, 0, 0, 0);
+                            uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+                            uint32_t nh[4], nl[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float q = __uint_as_float(hw[j] << 16) + __uint_as_float(lw[j] << 16);
+                                const float u = __uint_as_float(hw[j] & 0xffff0000u) + __uint_as_float(lw[j] & 0xffff0000u);
+                                const int ci = 4 * ch + j;
+                                const float4 tv = t[ci >> 1];
+                                const float tr = (ci & 1) ? tv.z : tv.x, ti = (ci & 1) ? tv.w : tv.y;
+                                const float qr = fmaf(q, tr, -u * ti), ur = fmaf(q, ti, u * tr);
+                                split_pair_bf16(qr, ur, nh[j], nl[j]);
+                            }
+                            *reinterpret_cast<uint4 *>(st + off) = make_uint4(nh[0], nh[1], nh[2], nh[3]);
+                            if (split) *reinterpret_cast<uint4 *>(st + kStageA + off) = make_uint4(nl[0], nl[1], nl[2], nl[3]);
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&S.conv[s]));
+                    if (++s == P.stages) { s = 0; ph ^= 1; }
+                }
+        }
+    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kNumEpiWarps) {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;
         const int h = (warp - kEpiWarp0) >> 2;
@@ -371,11 +489,11 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         uint32_t tph = 0;
         int g_all = 0, mt_count = 0;
         bool ok = true;
-        float master[kHalf];
+        float master[HALF];
         for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count) {
             const int64_t row = mt * kTileM + 32 * q + lane;
             float scale = P.out_scale;
-            if (P.rexp != nullptr && row < P.nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
+            if (P.rexp != nullptr && row < nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
             float bm = -1.0f;
             int bi = INT_MAX;
             for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
@@ -388,19 +506,19 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                     tph ^= 1u << b;
                     tc_fence_after();
                     const uint32_t taddr =
-                        tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kAccStride + h * kHalf);
+                        tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kAccStride + h * HALF);
 #pragma unroll
-                    for (int c0 = 0; c0 < kHalf; c0 += 32) {
+                    for (int c0 = 0; c0 < HALF; c0 += 32) {
                         uint32_t r[4][8];
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            if (c0 + 8 * j < kHalf) tmem_ld8(taddr + c0 + 8 * j, r[j]);
+                            if (c0 + 8 * j < HALF) tmem_ld8(taddr + c0 + 8 * j, r[j]);
                         tmem_wait_ld();
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
 #pragma unroll
                             for (int e = 0; e < 8; ++e)
-                                if (c0 + 8 * j < kHalf) {
+                                if (c0 + 8 * j < HALF) {
                                     const float v = __uint_as_float(r[j][e]);
                                     master[c0 + 8 * j + e] = g == 0 ? v : __fadd_rn(master[c0 + 8 * j + e], v);
                                 }
@@ -410,10 +528,10 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                     if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
                 }
                 if (!ok) break;
-                const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * kHalf;
-                const int kbase = (nt * P.tile_n + h * kHalf) >> 1;
+                const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * HALF;
+                const int kbase = (nt * P.tile_n + h * HALF) >> 1;
 #pragma unroll
-                for (int p = 0; p < kHalf / 2; ++p) {
+                for (int p = 0; p < HALF / 2; ++p) {
                     const float fr = master[2 * p] * scale, fi = master[2 * p + 1] * scale;
                     master[2 * p] = fr;
                     master[2 * p + 1] = fi;
@@ -425,24 +543,25 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 }
                 if (P.F != nullptr) {
 #pragma unroll
-                    for (int c0 = 0; c0 < kHalf; c0 += kEpiCols) {
+                    for (int c0 = 0; c0 < HALF; c0 += kEpiCols) {
 #pragma unroll
                         for (int j = 0; j < kEpiCols; ++j)
-                            if (c0 + j < kHalf) stg[lane * kEpiLd + j] = master[c0 + j];
+                            if (c0 + j < HALF) stg[lane * kEpiLd + j] = master[c0 + j];
                         __syncwarp();
                         // 4 lanes per row (one complex each), 8 rows per store instruction
                         const int jj = (lane & 3) * 2;
                         const int kk = kbase + (c0 >> 1) + (lane & 3);
-                        const bool colok = c0 + jj < min(ncols, kHalf) && kk < P.nphi;
+                        const bool colok = c0 + jj < min(ncols, HALF) && kk < P.nphi;
 #pragma unroll
                         for (int it = 0; it < 4; ++it) {
                             const int r = 8 * it + (lane >> 2);
                             const int64_t grow = mt * kTileM + 32 * q + r;
-                            if (colok && grow < P.nlos) {
+                            if (colok && grow < nlos) {
+                                const int64_t orow = P.rows ? P.rows[grow] : grow;
                                 const float2 val = make_float2(stg[r * kEpiLd + jj], stg[r * kEpiLd + jj + 1]);
                                 // streaming store: F is written once and must not push the
                                 // operands out of L2
-                                __stcs(reinterpret_cast<float2 *>(P.F + grow * row_pitch + 2 * (int64_t)kk), val);
+                                __stcs(reinterpret_cast<float2 *>(P.F + orow * row_pitch + 2 * (int64_t)kk), val);
                             }
                         }
                         __syncwarp();
@@ -468,11 +587,12 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 __syncwarp();
                 if (lane == 0) mbar_arrive(ebar);
                 if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; }
-                if (row < P.nlos) {
+                if (row < nlos) {
+                    const int64_t orow = P.rows ? P.rows[row] : row;
                     const bool found = bi != INT_MAX;
-                    if (P.pidx) P.pidx[row] = found ? bi : -1;
-                    if (P.pabs) P.pabs[row] = found ? sqrtf(bm) : __int_as_float(0x7fc00000);
-                    if (P.pphi) P.pphi[row] = found ? P.phi32[bi] : __int_as_float(0x7fc00000);
+                    if (P.pidx) P.pidx[orow] = found ? bi : -1;
+                    if (P.pabs) P.pabs[orow] = found ? sqrtf(bm) : __int_as_float(0x7fc00000);
+                    if (P.pphi) P.pphi[orow] = found ? P.phi32[bi] : __int_as_float(0x7fc00000);
                 }
             }
         }
@@ -492,8 +612,13 @@ size_t gemm_fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 8 + 8 * 3
 int gemm_stages(int tile_n, int mode)
 {
     size_t st = gemm_stage_bytes(tile_n, mode);
-    int s = (int)((kSmemLimit - gemm_fixed_smem()) / (st + 16));
+    int s = (int)((kSmemLimit - gemm_fixed_smem()) / (st + 24));
     return s > 8 ? 8 : s;
+}
+
+int mode_of(int precision)
+{
+    return precision == RMS_BF16 ? MODE_BF16 : (precision == RMS_BF16X3 ? MODE_BF16X3 : MODE_FP16X3);
 }
 
 }  // namespace
@@ -504,56 +629,73 @@ size_t split_operand_bytes(const rms_plan_s &p, int64_t nlos, int layout)
     return (size_t)((nlos + kTileM - 1) / kTileM) * kb * (2 * kStageA);
 }
 
-cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
-                              float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
-                              cudaStream_t s)
+cudaError_t launch_split(const rms_plan_s &p, const SplitOpts &o, cudaStream_t s)
 {
-    const bool chan = layout == RMS_CHAN_MAJOR;
-    const int mode = p.precision == RMS_BF16 ? MODE_BF16 : (p.precision == RMS_BF16X3 ? MODE_BF16X3 : MODE_FP16X3);
-    const int64_t nmt = (nlos + kTileM - 1) / kTileM;
+    const bool chan = o.layout == RMS_CHAN_MAJOR;
+    const int64_t nmt = (o.nout + kTileM - 1) / kTileM;
     if (nmt < 1) return cudaSuccess;
     if (nmt > 0x7fffffff) return cudaErrorInvalidValue;
-
     SplitParams sp;
-    sp.Q = Q;
-    sp.U = U;
-    sp.nlos = nlos;
+    sp.Q = o.Q;
+    sp.U = o.U;
+    sp.nlos_src = o.nlos_src;
+    sp.nout = o.nout;
+    sp.rows = o.rows;
+    sp.count = o.count;
     sp.nchan = p.nchan;
-    sp.layout = layout;
+    sp.layout = o.layout;
     sp.nk = chan ? p.nact : p.nchan;
     sp.kblocks = chan ? p.kblocks : p.kblocks_raw;
-    sp.mode = mode;
+    sp.mode = o.mode >= 0 ? o.mode : mode_of(p.precision);
     sp.active = p.d_active;
     sp.kbmask = p.d_kbmask;
-    sp.A = A;
-    sp.rexp = rexp;
-    sp.vec4 = !chan && (p.nchan % 4 == 0) && !(reinterpret_cast<uintptr_t>(Q) & 15) &&
-              !(reinterpret_cast<uintptr_t>(U) & 15);
+    sp.A = o.A;
+    sp.rexp = o.rexp;
+    sp.rscale = o.rscale;
+    sp.nact_norm = p.nact;
+    sp.vec4 = !chan && (p.nchan % 4 == 0) && !(reinterpret_cast<uintptr_t>(o.Q) & 15) &&
+              !(reinterpret_cast<uintptr_t>(o.U) & 15);
+    if (sp.mode == MODE_FP16X3 && !o.rexp) return cudaErrorInvalidValue;
     split_kernel<<<(unsigned)nmt, 128, 0, s>>>(sp);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
 
+cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
+{
+    const bool chan = o.layout == RMS_CHAN_MAJOR;
+    const int mode = mode_of(p.precision);
+    const int64_t nmt = (o.nlos + kTileM - 1) / kTileM;
+    if (nmt < 1) return cudaSuccess;
+    const bool rot = o.T != nullptr;
+    if (rot && (mode == MODE_FP16X3 || p.tile_n > 2 * kHalfRot || !o.centre)) return cudaErrorInvalidValue;
     GemmParams P;
-    P.A = A;
-    P.nlos = nlos;
-    P.kblocks = sp.kblocks;
+    P.A = o.A;
+    P.nlos = o.nlos;
+    P.count = o.count;
+    P.rows = o.rows;
+    P.kblocks = chan ? p.kblocks : p.kblocks_raw;
     int ngroups = (P.kblocks + kGroupKBlocks - 1) / kGroupKBlocks;
     P.group = (P.kblocks + ngroups - 1) / ngroups;
     P.nphi = p.nphi;
     P.ntiles_n = p.ntiles_n;
     P.tile_n = p.tile_n;
     P.tile_n_last = p.tile_n_last;
-    P.F = F;
-    P.pidx = pidx;
-    P.pabs = pabs;
-    P.pphi = pphi;
+    P.F = o.F;
+    P.pidx = o.pidx;
+    P.pabs = o.pabs;
+    P.pphi = o.pphi;
     P.phi32 = p.d_phi32;
     P.out_scale = (float)(p.K * p.wmax);
     P.mode = mode;
-    P.rexp = mode == MODE_FP16X3 ? rexp : nullptr;
+    P.rexp = mode == MODE_FP16X3 ? o.rexp : nullptr;
     P.err = p.d_err;
     P.timeout_ns = p.timeout_ns;
     P.stages = gemm_stages(p.tile_n, mode);
+    P.centre = o.centre;
+    P.T = o.T;
+    P.ldT = o.ldT;
+    P.cmin = o.cmin;
+    P.cmax = o.cmax;
     // RMS_L2_PREFETCH=1 turns on the L2 prefetch of the next M tile's operand (off by
     // default: on the LOFAR cube it evicted the current M tile's operand and cost 6%)
     static const int prefetch = [] {
@@ -562,15 +704,64 @@ cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *
     }();
     P.prefetch = prefetch;
     if (P.stages < 2) return cudaErrorInvalidConfiguration;
-    size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(p.tile_n, mode) + 16 * (size_t)P.stages;
-    e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(p.tile_n, mode) + 24 * (size_t)P.stages;
     int ctas = p.num_sms;
     if (const char *v = std::getenv("RMS_GEMM_CTAS")) {   // tuning knob: persistent CTAs
         int c = std::atoi(v);
         if (c >= 1 && c <= p.num_sms) ctas = c;
     }
     int grid = (int)(nmt < ctas ? nmt : ctas);
-    gemm_kernel<<<grid, kThreads, smem, s>>>(P, chan ? p.tmap_bhi : p.tmap_bhi_raw, chan ? p.tmap_blo : p.tmap_blo_raw);
+    const CUtensorMap &bhi = chan ? p.tmap_bhi : p.tmap_bhi_raw, &blo = chan ? p.tmap_blo : p.tmap_blo_raw;
+    cudaError_t e;
+    if (rot) {
+        auto kern = gemm_kernel<kHalfRot, true>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 512, smem, s>>>(P, bhi, blo);
+    } else {
+        if (p.tile_n > 2 * kHalf) return cudaErrorInvalidValue;
+        auto kern = gemm_kernel<kHalf, false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kThreads, smem, s>>>(P, bhi, blo);
+    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *src, const int64_t *rows,
+                                const int64_t *count, int64_t nmax, uint8_t *dst, cudaStream_t s)
+{
+    const int64_t nmt = (nmax + kTileM - 1) / kTileM;
+    if (nmt < 1) return cudaSuccess;
+    if (nmt > 0x7fffffff) return cudaErrorInvalidValue;
+    const int kb = layout == RMS_CHAN_MAJOR ? p.kblocks : p.kblocks_raw;
+    const int parts = p.precision == RMS_BF16 ? 1 : 2;
+    image_gather_kernel<<<(unsigned)nmt, 128, 0, s>>>(src, dst, kb, rows, count, nmax, parts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
+                              float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
+                              cudaStream_t s)
+{
+    SplitOpts so;
+    so.Q = Q;
+    so.U = U;
+    so.nlos_src = nlos;
+    so.nout = nlos;
+    so.layout = layout;
+    so.A = A;
+    so.rexp = rexp;
+    cudaError_t e = launch_split(p, so, s);
+    if (e != cudaSuccess) return e;
+    GemmOpts go;
+    go.A = A;
+    go.nlos = nlos;
+    go.layout = layout;
+    go.F = F;
+    go.pidx = pidx;
+    go.pabs = pabs;
+    go.pphi = pphi;
+    go.rexp = rexp;
+    return launch_gemm(p, go, s);
 }

@@ -9,6 +9,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "rms_internal.h"
 
 namespace {
@@ -39,6 +41,26 @@ __global__ void phase_table_kernel(const double *__restrict__ dl2, const double 
         double s, c;
         phase_sincos(phi[k], dl2[a], &s, &c);
         tab[t] = make_float2((float)(w[a] * c), (float)(w[a] * s));
+    }
+}
+
+// Window rotation table [ncentre][ld]: T[n][j] = exp(-2i phi_n dl2_j) with
+// phi_n = phi0 + n step (FP64 argument, reduced as above), FP32 complex;
+// columns j >= nk (padding) hold 1.
+__global__ void rotation_table_kernel(const double *__restrict__ dl2, int32_t nk, int32_t ld, double phi0,
+                                      double step, int32_t ncentre, float2 *__restrict__ T)
+{
+    int64_t total = (int64_t)ncentre * ld;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t n = (int32_t)(t / ld), j = (int32_t)(t % ld);
+        if (j >= nk) {
+            T[t] = make_float2(1.f, 0.f);
+            continue;
+        }
+        double s, c;
+        phase_sincos(phi0 + n * step, dl2[j], &s, &c);
+        T[t] = make_float2((float)c, (float)-s);
     }
 }
 
@@ -162,5 +184,15 @@ cudaError_t launch_rmsf(const rms_plan_s &p, const double *d_phi, int32_t n, dou
     if (n <= 0) return cudaSuccess;
     rmsf_kernel<<<(n + 127) / 128, 128, 0, s>>>(p.d_dl2, p.d_wact, p.nact, p.K, d_phi, n, d_R64,
                                                  d_R32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rotation_table(const double *dl2, int32_t nk, int32_t ld, double phi0, double step,
+                                  int32_t ncentre, float2 *T, cudaStream_t s)
+{
+    const int64_t total = (int64_t)ncentre * ld;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8192);
+    if (blocks < 1) return cudaSuccess;
+    rotation_table_kernel<<<blocks, 256, 0, s>>>(dl2, nk, ld, phi0, step, ncentre, T);
     return cudaGetLastError();
 }

@@ -45,6 +45,7 @@ struct rms_plan_s {
     // LOS-major cubes contract over all channels (flagged ones zeroed in the
     // converter, zero rows in B), so their data tiles are contiguous boxes
     double *d_dl2_all = nullptr;   // [nchan]
+    double *d_lambda2_all = nullptr;  // [nchan] lambda_j^2 (source generator)
     double *d_w_all = nullptr;     // [nchan]
     uint16_t *d_bhi_raw = nullptr, *d_blo_raw = nullptr;   // [npad][kpad_raw]; alias d_bhi/d_blo if no flags
     uint16_t *d_kbmask = nullptr;  // [kblocks_raw] bit i: channel 16 kb + i is active
@@ -77,6 +78,8 @@ struct rms_plan_s {
 cudaError_t launch_phase_table(const rms_plan_s &p, cudaStream_t s);
 cudaError_t launch_phase_bsplit(const rms_plan_s &p, const double *dl2, const double *w, int32_t nk,
                                 int32_t kpad, uint16_t *bhi, uint16_t *blo, bool fp16, cudaStream_t s);
+cudaError_t launch_rotation_table(const double *dl2, int32_t nk, int32_t ld, double phi0, double step,
+                                  int32_t ncentre, float2 *T, cudaStream_t s);
 cudaError_t launch_rmsf(const rms_plan_s &p, const double *d_phi, int32_t n, double *d_R64,
                         float *d_R32, cudaStream_t s);
 
@@ -93,10 +96,79 @@ cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float
                                 int layout, int8_t *rexp, cudaStream_t s);
 
 // gemm.cu: split kernel (layout stage) + contraction kernel
+// Split operand image: [ceil(rows / 128)][kblocks][16 KB], K blocks of 16 channels
+// (kblocks of the plan for channel-major cubes, kblocks_raw for LOS-major ones).
 size_t split_operand_bytes(const rms_plan_s &p, int64_t nlos, int layout);
+struct SplitOpts {
+    const float *Q = nullptr, *U = nullptr;
+    int64_t nlos_src = 0;              // lines of sight in the cube
+    int layout = RMS_CHAN_MAJOR;
+    int64_t nout = 0;                  // rows of the image (grid size)
+    const int64_t *rows = nullptr;     // optional gather: image row r <- cube row rows[r]
+    const int64_t *count = nullptr;    // optional device count of image rows to fill
+    int mode = -1;                     // -1: the plan's precision; 0 BF16 (hi only)
+    uint8_t *A = nullptr;
+    int8_t *rexp = nullptr;            // FP16X3 per-row exponents
+    float *rscale = nullptr;           // optional per-row 1 / RMS of |P| over the active channels
+};
+struct GemmOpts {
+    const uint8_t *A = nullptr;
+    int64_t nlos = 0;                  // image rows
+    const int64_t *count = nullptr;    // optional device count (<= nlos) of live rows
+    const int64_t *rows = nullptr;     // optional scatter of results: row r -> rows[r]
+    int layout = RMS_CHAN_MAJOR;
+    float *F = nullptr;
+    int32_t *pidx = nullptr;
+    float *pabs = nullptr, *pphi = nullptr;
+    const int8_t *rexp = nullptr;
+    // window plans: rotate row r by T[clamp(centre[r], cmin, cmax)][.] ([.][ldT] float2)
+    const int32_t *centre = nullptr;
+    const float2 *T = nullptr;
+    int32_t ldT = 0, cmin = 0, cmax = 0;
+};
+cudaError_t launch_split(const rms_plan_s &p, const SplitOpts &o, cudaStream_t s);
+cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s);
+cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *src, const int64_t *rows,
+                                const int64_t *count, int64_t nmax, uint8_t *dst, cudaStream_t s);
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
                               cudaStream_t s);
+
+// generate.cu
+cudaError_t launch_generate(const rms_plan_s &p, const rms_source_model &m, int64_t los0, int64_t nlos,
+                            int32_t layout, float *Q, float *U, cudaStream_t s);
+
+// net.cu: the learned proposal's network
+struct rms_net_s {
+    rms_plan_s *plan = nullptr;
+    int device = 0;
+    int32_t nin = 0, hidden = 0, nbins = 0, nbp = 0, max_batch = 0, ldb = 0;
+    int64_t nparams = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, steps = 0;
+    float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;   // flat FP32 (W1, b1, W2, b2)
+    uint16_t *d_W1c = nullptr;   // [hidden][kpad]: W1 in the column order of channel-major operand images
+    uint16_t *d_W1r = nullptr;   // [hidden][kpad_raw]: LOS-major images (zero columns for flagged channels)
+    uint16_t *d_W2 = nullptr;    // [nbins][hidden]
+    uint16_t *d_W2T = nullptr;   // [hidden][nbp]
+    int32_t *d_colmap_c = nullptr, *d_colmap_r = nullptr;   // image column -> W1 column, -1 for none
+    CUtensorMap tm_W1c, tm_W1r, tm_W2, tm_W2T;
+    // training scratch for max_batch lines of sight
+    uint8_t *d_img = nullptr;
+    float *d_rs = nullptr, *d_dz32 = nullptr, *d_da32 = nullptr, *d_loss = nullptr;
+    uint16_t *d_h = nullptr, *d_hT = nullptr, *d_dz = nullptr, *d_dzT = nullptr, *d_da1T = nullptr, *d_XT = nullptr;
+    cudaEvent_t last = nullptr;
+};
+// Network forward from a split image (hi parts) and its per-row 1/RMS: bin and
+// confidence (window mass within halfwin bins; < 0: largest probability), logits
+// optional.  h: [nlos][hidden] BF16 scratch.
+cudaError_t net_forward_image(const rms_net_s &n, const uint8_t *img, int layout, const float *rscale, int64_t nlos,
+                              uint16_t *h, float *logits, int32_t *bin, float *conf, int32_t halfwin,
+                              cudaStream_t s);
+
+// api.cu: plan creation with a cap on phase rows per tensor-core tile (window
+// plans use 128, the rotating kernel's limit)
+rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nchan, int32_t axis_kind,
+                                const double *weights, const double *phi, int32_t nphi, int32_t precision,
+                                int32_t device, int32_t max_tile_cap);
 
 // api.cu: cuTensorMapEncodeTiled through the runtime's driver entry point
 bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, void *base, const cuuint64_t *dims,
