@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-paths", action="store_true", help="skip timing the other precision paths")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n-train", type=int, default=1 << 20, help="learned workload: training LOS")
+    ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
+    ap.add_argument("--hidden", type=int, default=256, help="learned workload: hidden units")
     return ap.parse_args()
 
 
@@ -387,10 +390,167 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+LEARNED_METRIC = "learned peak map: full-grid-equivalent G(LOS*chan*phi)/s at >=99.5% phi_peak agreement"
+
+
+def run_learned(args):
+    """The learned proposal on the learned workload (2048^2 LOS, LOFAR band, SNR 5-100).
+
+    The network is trained here on the GPU (1M generated LOS labelled by the
+    full grid), its confidence threshold calibrated on a separate validation set,
+    then one step = one rms_peakmap_learned call over the cube (device-resident
+    FP32 Q/U in, peak map out), timed next to the full-grid peak map
+    (rms_synth, peak map only) at the same precision and at plain BF16."""
+    import torch
+    import paper_1810_06250_gb300 as rms
+    from paper_1810_06250_gb300 import inputs, learned as Lm
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rms.build()
+    cfg = inputs.CONFIGS["learned"]
+    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
+    nact = int(np.count_nonzero(w))
+    L = cfg.nlos
+    plan = rms.Plan(freq, phi, args.path, weights=w, device=local)
+    t0 = time.perf_counter()
+    net = Lm.Net(plan, hidden=args.hidden, max_batch=4096, seed=101)
+    win = Lm.Window(plan, 64)
+    hist = Lm.train(plan.handle, net, cfg, n_train=args.n_train, epochs=args.epochs, batch=4096, seed=5001 + rank)
+    tau, cal = Lm.calibrate(plan.handle, net, win, cfg, n_val=1 << 18, seed=6001 + rank, layout=args.layout)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    Q, U = Lm.generate(plan.handle, cfg, 0, L, args.layout, seed=cfg.seed + 1000 * rank)
+    stream = torch.cuda.Stream(dev)
+    php = torch.empty(L, device=dev)
+    pka = torch.empty(L, device=dev)
+    fb = torch.empty(L, dtype=torch.int32, device=dev)
+    nfb = torch.zeros(1, dtype=torch.int64, device=dev)
+    fidx = torch.empty(L, dtype=torch.int32, device=dev)
+    fphi = torch.empty(L, device=dev)
+    fabs = torch.empty(L, device=dev)
+    units = L * nact * cfg.nphi
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        barrier = dist.barrier
+
+    def learned_step():
+        rms.rms_peakmap_learned(win.handle, net.handle, Q, U, L, args.layout, tau, php, pka, fb, nfb, stream)
+
+    def full_step():
+        plan.synth(Q, U, L, args.layout, None, fidx, fabs, fphi, stream)
+
+    with torch.cuda.stream(stream):
+        with ClockSampler(local) as clk:
+            t_learn, per = time_steps(learned_step, stream, args.steps, args.warmup, torch, barrier)
+        t_full, _ = time_steps(full_step, stream, max(3, args.steps // 2), 2, torch)
+        with rms.Plan(freq, phi, "bf16", weights=w, device=local) as p1:
+            def bf16_step():
+                p1.synth(Q, U, L, args.layout, None, fidx, fabs, fphi, stream)
+            t_bf16, _ = time_steps(bf16_step, stream, max(3, args.steps // 2), 2, torch)
+        full_step()
+        learned_step()
+    torch.cuda.synchronize()
+    plan.sync(stream)
+    ms_learn = t_learn / args.steps
+    ms_full = t_full / max(3, args.steps // 2)
+    ms_bf16 = t_bf16 / max(3, args.steps // 2)
+    agree = float(np.mean(np.abs(php.cpu().numpy().astype(np.float64) - fphi.cpu().numpy()) <= 0.5 * (1 + 1e-6)))
+    fbr = float(fb.cpu().numpy().mean())
+    t = torch.tensor([t_learn], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    value = world * units * args.steps / (tmax * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6701.0)
+    in_bytes = L * 8.0 * (nact if args.layout == "chan" else cfg.nchan)
+    alg = in_bytes + 8.0 * L
+    line = {"metric": LEARNED_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.path, "data": "synthetic",
+            "config": {"workload": "learned: 2048x2048 LOS x 400 channels (%d active) 115-178 MHz x 401 phi in "
+                                   "[-100, 100], FP32 Q/U %s-major, peak map only; 1-3 thin/Burn-slab components, "
+                                   "SNR 5-100; window 64 x 0.25 rad/m^2" % (nact, args.layout),
+                       "nlos_per_gpu": L, "l2": "inputs larger than L2 (13.4 GB per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "learned": {"speedup_vs_full_grid_same_precision": ms_full / ms_learn,
+                        "speedup_vs_full_grid_bf16": ms_bf16 / ms_learn,
+                        "ms_learned": ms_learn, "ms_full_grid": ms_full, "ms_full_grid_bf16": ms_bf16,
+                        "agreement": agree, "fallback_frac": fbr, "tau": tau, "val_fallback_frac": cal["fallback_frac"],
+                        "train_loss": hist, "train_s": train_s, "n_train": args.n_train, "epochs": args.epochs,
+                        "hidden": args.hidden,
+                        "params": int(net.nparams), "flop_per_los": 2 * (net.nparams - args.hidden - cfg.nphi)},
+            "roofline": {"bound": "hbm", "achieved": alg / (ms_learn * 1e-3) / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": alg / (ms_learn * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                         "algorithmic": "cube read once (8 B per LOS x contraction channel) + 8 B peak map per LOS",
+                         "peak_source": "measured HBM copy (MEASURED_PEAKS.json)"},
+            "gpu_launches": args.steps * 9, "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_e2e:
+        Qh = torch.empty(Q.shape, dtype=torch.float32).pin_memory()
+        Uh = torch.empty(U.shape, dtype=torch.float32).pin_memory()
+        Qh.copy_(Q)
+        Uh.copy_(U)
+        ph_h = torch.empty(L).pin_memory()
+        pa_h = torch.empty(L).pin_memory()
+
+        def e2e():
+            with torch.cuda.stream(stream):
+                Q.copy_(Qh, non_blocking=True)
+                U.copy_(Uh, non_blocking=True)
+                learned_step()
+                ph_h.copy_(php, non_blocking=True)
+                pa_h.copy_(pka, non_blocking=True)
+            stream.synchronize()
+        e2e()
+        n_e2e = 3
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e()
+        dt = (time.perf_counter() - t0) / n_e2e
+        line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
+                       "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(L * 8),
+                       "how": "pinned host Q/U -> device, rms_peakmap_learned, phi_peak and |F|_peak -> pinned host"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        op = oracle.plan(freq, "freq", w)
+        Qc, Uc = inputs.make_cube(cfg, 0, 2048)
+        t0 = time.perf_counter()
+        oracle.synth(Qc[:128], Uc[:128], op, phi)
+        per_los = (time.perf_counter() - t0) / 128
+        n = int(min(2048, max(128, args.cpu_seconds / per_los)))
+        t0 = time.perf_counter()
+        oracle.peak(oracle.synth(Qc[:n], Uc[:n], op, phi))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n * nact * cfg.nphi / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": "full-grid FP64 peak map of %d of %d LOS, %.1f s"
+                                % (n, L, dt)}
+    net.close()
+    win.close()
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -28,6 +28,7 @@
 struct rms_window_s {
     rms_plan_s *plan = nullptr;   // the full-grid plan
     rms_plan_s *sub = nullptr;    // same channels, phi = the window offsets
+    int device = 0;
     int32_t width = 0, ncentre = 0, cmin = 0, cmax = 0;
     double phi0 = 0, step = 0;    // fine grid phi_0 + n step, step = D / 2
     float2 *d_Tc = nullptr;       // [ncentre][ldc], active-channel order (channel-major images)
@@ -154,6 +155,7 @@ rms_status rms_window_create(rms_window_t *out, rms_plan_t plan, int32_t width)
     rms_window_s *w = new (std::nothrow) rms_window_s();
     if (!w) return RMS_ERR_OOM;
     w->plan = plan;
+    w->device = p.device;
     w->width = width;
     w->step = D / 2;
     w->phi0 = p.phi[0];
@@ -196,7 +198,7 @@ rms_status rms_window_create(rms_window_t *out, rms_plan_t plan, int32_t width)
 rms_status rms_window_destroy(rms_window_t w)
 {
     if (!w) return RMS_OK;
-    Guard guard(w->plan->device);
+    Guard guard(w->device);   // the parent plan may already be gone: only the window's own state is used
     cudaDeviceSynchronize();
     free_window(w);
     return RMS_OK;

@@ -29,11 +29,16 @@ def source_model(cfg: CubeConfig, seed: int | None = None) -> B.rms_source_model
     return m
 
 
-class Net:
-    """Owns one rms_net_t."""
+def _handle(plan):
+    return plan if isinstance(plan, int) else plan.handle
 
-    def __init__(self, plan: int, hidden: int = 256, max_batch: int = 4096, seed: int = 1):
-        self.handle = B.rms_net_create(plan, hidden, max_batch, seed)
+
+class Net:
+    """Owns one rms_net_t; keeps the plan object it was built on alive."""
+
+    def __init__(self, plan, hidden: int = 256, max_batch: int = 4096, seed: int = 1):
+        self.plan = plan
+        self.handle = B.rms_net_create(_handle(plan), hidden, max_batch, seed)
         self.nparams = B.rms_net_info(self.handle, B.RMS_NET_NPARAMS)
         self.max_batch = max_batch
         self.hidden = hidden
@@ -64,10 +69,11 @@ class Net:
 
 
 class Window:
-    """Owns one rms_window_t."""
+    """Owns one rms_window_t; keeps the plan object it was built on alive."""
 
-    def __init__(self, plan: int, width: int = 64):
-        self.handle = B.rms_window_create(plan, width)
+    def __init__(self, plan, width: int = 64):
+        self.plan = plan
+        self.handle = B.rms_window_create(_handle(plan), width)
         self.width = width
 
     @property
