@@ -179,23 +179,28 @@ __global__ void __launch_bounds__(128) image_gather_kernel(const uint8_t *src, u
                                                            int64_t nmax, int32_t parts)
 {
     const int m = threadIdx.x;
+    const int kb = blockIdx.y;
     const int64_t j = (int64_t)blockIdx.x * kTileM + m;
     const int64_t n = min(*count, nmax);
     if ((int64_t)blockIdx.x * kTileM >= n) return;
     if (j >= n) return;
     const int64_t r = rows[j];
     const int ms = (int)(r % kTileM), swd = (m >> 1) & 3, sws = (ms >> 1) & 3;
-    const uint8_t *sb = src + (size_t)(r / kTileM) * kblocks * (2 * kStageA);
-    uint8_t *db = dst + (size_t)blockIdx.x * kblocks * (2 * kStageA);
-    for (int kb = 0; kb < kblocks; ++kb)
-        for (int part = 0; part < parts; ++part) {
-            const size_t base = (size_t)kb * (2 * kStageA) + (size_t)part * kStageA;
+    const uint8_t *sb = src + ((size_t)(r / kTileM) * kblocks + kb) * (2 * kStageA);
+    uint8_t *db = dst + ((size_t)blockIdx.x * kblocks + kb) * (2 * kStageA);
+    uint4 v[2][4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(sb + base + ms * kRowBytes + ((c ^ sws) << 4));
-                *reinterpret_cast<uint4 *>(db + base + m * kRowBytes + ((c ^ swd) << 4)) = v;
-            }
-        }
+    for (int part = 0; part < 2; ++part)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (part < parts)
+                v[part][c] = *reinterpret_cast<const uint4 *>(sb + part * kStageA + ms * kRowBytes + ((c ^ sws) << 4));
+#pragma unroll
+    for (int part = 0; part < 2; ++part)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (part < parts)
+                *reinterpret_cast<uint4 *>(db + part * kStageA + m * kRowBytes + ((c ^ swd) << 4)) = v[part][c];
 }
 
 // ----------------------------------------------------------------------------
@@ -442,11 +447,15 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             int c = P.cmin;
             if (live) c = max(P.cmin, min(P.cmax, P.centre[row]));
             const float4 *trow = reinterpret_cast<const float4 *>(P.T + (size_t)c * P.ldT);
+            // T for the next K block is loaded while this one is rotated (L2 latency hidden)
+            float4 t[8], tn[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) t[v] = live ? __ldg(trow + v) : make_float4(1.f, 0.f, 1.f, 0.f);
             for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
                 for (int kb = 0; kb < P.kblocks; ++kb) {
-                    float4 t[8];
+                    const int kbn = kb + 1 < P.kblocks ? kb + 1 : 0;
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) t[v] = live ? __ldg(trow + kb * 8 + v) : make_float4(1.f, 0.f, 1.f, 0.f);
+                    for (int v = 0; v < 8; ++v) tn[v] = live ? __ldg(trow + kbn * 8 + v) : make_float4(1.f, 0.f, 1.f, 0.f);
                     if (!warp_wait(smem_u32(&S.full[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
                         ok = false;
                         break;
@@ -478,6 +487,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&S.conv[s]));
                     if (++s == P.stages) { s = 0; ph ^= 1; }
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) t[v] = tn[v];
                 }
         }
     } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kNumEpiWarps) {
@@ -736,7 +747,8 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
     if (nmt > 0x7fffffff) return cudaErrorInvalidValue;
     const int kb = layout == RMS_CHAN_MAJOR ? p.kblocks : p.kblocks_raw;
     const int parts = p.precision == RMS_BF16 ? 1 : 2;
-    image_gather_kernel<<<(unsigned)nmt, 128, 0, s>>>(src, dst, kb, rows, count, nmax, parts);
+    if (kb > 65535) return cudaErrorInvalidValue;
+    image_gather_kernel<<<dim3((unsigned)nmt, (unsigned)kb), 128, 0, s>>>(src, dst, kb, rows, count, nmax, parts);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@
 //            column map from image columns to weight columns)
 //   warp 0      TMA / bulk producer                        -> full
 //   warp 1      TMEM allocator, single-thread MMA issuer   -> empty, tfull
-//   warps 4-7   epilogue, one accumulator row per thread   -> tempty
+//   warps 4-11  epilogue: warp w owns TMEM lane quarter w % 4 and column half
+//               (w - 4) / 4 of each accumulator row          -> tempty
 // Every wait is bounded (abort flag, device error word, drain, TMEM freed).
 #include <cuda_bf16.h>
 #include <math.h>
@@ -39,13 +40,14 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 enum { EPI_RELU = 0, EPI_SOFTMAX = 1, EPI_DRELU = 2, EPI_ACC = 3 };
-constexpr int kNetThreads = 256;
-constexpr int kNetEpiWarp0 = 4;
+constexpr int kNetThreads = 384;
+constexpr int kNetEpiWarp0 = 4;    // warps 4-11: two per TMEM lane quarter, one per column half
 constexpr int kNetTmemCols = 512;
 constexpr int kNetStageA = kTileM * 64;       // 8 KB: 128 rows x 32 BF16
 constexpr int kImageKBlockBytes = 2 * kNetStageA;   // split image: hi then lo per K block
 constexpr int kNetSmemLimit = 227 * 1024;
-constexpr int kNetFixedSmem = 1024 + 256;
+constexpr int kNetXchFloats = 4 * kTileM;     // (max, sum, argmax, z_label) per row
+constexpr int kNetFixedSmem = 1024 + 256 + kNetXchFloats * 4;
 
 struct NetGemmParams {
     int32_t M, N, kblocks, kb_per_split, ksplit, mtiles, ntiles;
@@ -79,6 +81,7 @@ struct NSmem {
     uint64_t *full, *empty, *tfull, *tempty, *mma_done;
     uint32_t *tmem_slot;
     volatile int *abort_flag;
+    float *xch;                 // softmax: per-row values exchanged between the two column halves
 };
 
 __device__ __forceinline__ NSmem ncarve(uint8_t *base, const NetGemmParams &P)
@@ -94,6 +97,7 @@ __device__ __forceinline__ NSmem ncarve(uint8_t *base, const NetGemmParams &P)
     s.mma_done = s.tempty + 2;
     s.tmem_slot = reinterpret_cast<uint32_t *>(s.mma_done + 1);
     s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
+    s.xch = reinterpret_cast<float *>(const_cast<int *>(s.abort_flag) + 2);
     return s;
 }
 
@@ -107,19 +111,22 @@ __device__ __forceinline__ void item_coords(const NetGemmParams &P, int64_t it, 
     kb1 = min(P.kblocks, kb0 + P.kb_per_split);
 }
 
-// 32 accumulator columns of this thread's row, starting at column c0 (fewer at the tile's end).
-__device__ __forceinline__ void load32(uint32_t taddr, int c0, int BN, float (&v)[32])
+// 32 accumulator columns of this thread's row, starting at column c0 (fewer before column end).
+__device__ __forceinline__ void load32(uint32_t taddr, int c0, int end, float (&v)[32])
 {
     uint32_t r[4][8];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-        if (c0 + 8 * j < BN) tmem_ld8(taddr + c0 + 8 * j, r[j]);
+        if (c0 + 8 * j < end) tmem_ld8(taddr + c0 + 8 * j, r[j]);
     tmem_wait_ld();
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[8 * j + e] = (c0 + 8 * j < BN) ? __uint_as_float(r[j][e]) : 0.f;
+        for (int e = 0; e < 8; ++e) v[8 * j + e] = (c0 + 8 * j < end) ? __uint_as_float(r[j][e]) : 0.f;
 }
+
+// The two warps that share a TMEM lane quarter (64 threads, named barrier 1 + q).
+__device__ __forceinline__ void pair_sync(int q) { asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
@@ -127,22 +134,27 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__device__ void epilogue(const NetGemmParams &P, uint32_t tacc, int mt, int nt, int q, int lane)
+// One accumulator row per thread; the warp pair of a lane quarter splits the
+// columns in halves [c_lo, c_hi).
+__device__ void epilogue(const NetGemmParams &P, const NSmem &SM, uint32_t tacc, int mt, int nt, int q, int h,
+                         int lane)
 {
     const int r = 32 * q + lane;
     const int64_t m = (int64_t)mt * kTileM + r;
     const bool valid = m < P.M;
     const float rs = (P.row_scale && valid) ? P.row_scale[m] : 1.0f;
     const int n_base = nt * P.BN;
+    const int half = P.BN / 2;
+    const int c_lo = h * half, c_hi = c_lo + half;
     float v[32];
     if (P.epi == EPI_RELU || P.epi == EPI_DRELU || P.epi == EPI_ACC) {
-        for (int c0 = 0; c0 < P.BN; c0 += 32) {
-            load32(tacc, c0, P.BN, v);
+        for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+            load32(tacc, c0, c_hi, v);
             if (!valid) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int n0 = n_base + c0 + 8 * j;
-                if (c0 + 8 * j >= P.BN || n0 >= P.N) continue;
+                if (c0 + 8 * j >= c_hi || n0 >= P.N) continue;
                 float o[8];
                 if (P.epi == EPI_RELU) {
 #pragma unroll
@@ -188,56 +200,120 @@ __device__ void epilogue(const NetGemmParams &P, uint32_t tacc, int mt, int nt, 
         return;
     }
     // ---------------------------------------------------------------- SOFTMAX
+    // One pass per half: running max, argmax (lowest index on ties) and the sum of
+    // exp(z - max), rescaled once per 32-column chunk; the halves then combine
+    // through shared memory.  A second pass touches only the confidence window.
     const bool train = P.label != nullptr;
-    float mx = -INFINITY;
-    int bi = -1;
-    for (int c0 = 0; c0 < P.BN; c0 += 32) {
-        load32(tacc, c0, P.BN, v);
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const int n = c0 + e;
-            if (n < P.N) {
-                const float z = v[e] + P.bias[n];
-                if (z > mx) { mx = z; bi = n; }
-                if (!train && P.outf && valid) P.outf[m * P.ldf + n] = z;
-            }
-        }
-    }
     const int y = (train && valid) ? P.label[m] : -1;
-    float S = 0.f, Sw = 0.f, zy = 0.f;
-    for (int c0 = 0; c0 < P.BN; c0 += 32) {
-        load32(tacc, c0, P.BN, v);
+    float mx = -INFINITY, S = 0.f, zy = 0.f;
+    int bi = -1;
+    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+        load32(tacc, c0, c_hi, v);
+        float cm = -INFINITY;
+        int ci = -1;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
             const int n = c0 + e;
-            if (n < P.N) {
-                const float z = v[e] + P.bias[n];
-                const float ez = expf(z - mx);
-                S += ez;
-                if (P.halfwin >= 0 && abs(n - bi) <= P.halfwin) Sw += ez;
-                if (n == y) zy = z;
+            if (n < c_hi && n < P.N) {
+                v[e] += P.bias[n];
+                if (v[e] > cm) { cm = v[e]; ci = n; }
+                if (n == y) zy = v[e];
+                if (!train && P.outf && valid) P.outf[m * P.ldf + n] = v[e];
+            }
+        }
+        if (cm > mx) {
+            S *= __expf(mx - cm);
+            mx = cm;
+            bi = ci;
+        }
+        if (mx > -INFINITY) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int n = c0 + e;
+                if (n < c_hi && n < P.N) S += __expf(v[e] - mx);
             }
         }
     }
-    if (valid) {
-        if (P.bin) P.bin[m] = max(bi, 0);
-        if (P.conf) P.conf[m] = P.halfwin >= 0 ? Sw / S : 1.0f / S;
+    float *X = SM.xch;   // [4][128]: max, sum, argmax, z_label
+    if (h == 1) {
+        X[r] = mx;
+        X[kTileM + r] = S;
+        X[2 * kTileM + r] = __int_as_float(bi);
+        X[3 * kTileM + r] = zy;
     }
-    if (!train) return;
-    float lrow = valid ? (logf(S) + mx - zy) : 0.f;
+    pair_sync(q);
+    if (h == 0) {
+        const float m1 = X[r], s1 = X[kTileM + r], z1 = X[3 * kTileM + r];
+        const int b1 = __float_as_int(X[2 * kTileM + r]);
+        const float M = fmaxf(mx, m1);
+        const float St = (mx > -INFINITY ? S * __expf(mx - M) : 0.f) + (m1 > -INFINITY ? s1 * __expf(m1 - M) : 0.f);
+        if (m1 > mx) bi = b1;
+        if (y >= c_hi) zy = z1;
+        mx = M;
+        S = St;
+        X[r] = mx;
+        X[kTileM + r] = S;
+        X[2 * kTileM + r] = __int_as_float(bi);
+    }
+    pair_sync(q);
+    if (h == 1) {
+        mx = X[r];
+        S = X[kTileM + r];
+        bi = __float_as_int(X[2 * kTileM + r]);
+    }
+    // window mass: columns within halfwin of the argmax that lie in this half.  The
+    // TMEM loads are warp-collective (.sync.aligned), so every lane walks the same
+    // 8-column groups -- those that meet any lane's window -- and masks its own.
+    float Sw = 0.f;
+    if (P.halfwin >= 0) {
+        const bool has = bi >= 0;
+        int w0 = has ? max(c_lo, bi - P.halfwin) : c_hi;
+        int w1 = has ? min(min(c_hi, P.N), bi + P.halfwin + 1) : c_lo;
+        int g0 = w0, g1 = w1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lrow += __shfl_xor_sync(0xffffffffu, lrow, o);
-    if (lane == 0 && P.loss) atomicAdd(P.loss, lrow * P.inv_batch);
+        for (int o = 16; o > 0; o >>= 1) {
+            g0 = min(g0, __shfl_xor_sync(0xffffffffu, g0, o));
+            g1 = max(g1, __shfl_xor_sync(0xffffffffu, g1, o));
+        }
+        for (int c0 = g0 & ~7; c0 < g1; c0 += 8) {
+            uint32_t rr[8];
+            tmem_ld8(tacc + c0, rr);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int n = c0 + e;
+                if (n >= w0 && n < w1) Sw += __expf(__uint_as_float(rr[e]) + P.bias[n] - mx);
+            }
+        }
+    }
+    pair_sync(q);
+    if (h == 1) X[r] = Sw;
+    pair_sync(q);
+    if (h == 0) {
+        Sw += X[r];
+        if (valid) {
+            if (P.bin) P.bin[m] = max(bi, 0);
+            if (P.conf) P.conf[m] = P.halfwin >= 0 ? Sw / S : 1.0f / S;
+        }
+        if (train) {
+            float lrow = valid ? (logf(S) + mx - zy) : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lrow += __shfl_xor_sync(0xffffffffu, lrow, o);
+            if (lane == 0 && P.loss) atomicAdd(P.loss, lrow * P.inv_batch);
+        }
+    }
+    pair_sync(q);   // the exchange buffer is reused by the next tile
+    if (!train) return;
     const float invS = 1.0f / S;
-    for (int c0 = 0; c0 < P.BN; c0 += 32) {
-        load32(tacc, c0, P.BN, v);
+    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+        load32(tacc, c0, c_hi, v);
         if (!valid) continue;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
             const int n = c0 + e;
-            if (n < P.N) {
+            if (n < c_hi && n < P.N) {
                 const float z = v[e] + P.bias[n];
-                const float d = (expf(z - mx) * invS - (n == y ? 1.f : 0.f)) * P.inv_batch;
+                const float d = (__expf(z - mx) * invS - (n == y ? 1.f : 0.f)) * P.inv_batch;
                 P.out[m * P.ldo + n] = __float2bfloat16_rn(d);
                 P.outT[(int64_t)n * P.ldt + m] = __float2bfloat16_rn(d);
                 P.outf[m * P.ldf + n] = d;
@@ -263,7 +339,7 @@ net_gemm_kernel(const __grid_constant__ NetGemmParams P, const __grid_constant__
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.tfull[b]), 1);
-            mbar_init(smem_u32(&S.tempty[b]), 4);
+            mbar_init(smem_u32(&S.tempty[b]), 8);
         }
         mbar_init(smem_u32(S.mma_done), 1);
         *S.abort_flag = 0;
@@ -361,7 +437,7 @@ net_gemm_kernel(const __grid_constant__ NetGemmParams P, const __grid_constant__
             }
         }
     } else if (warp >= kNetEpiWarp0) {
-        const int q = warp & 3;
+        const int q = warp & 3, h = (warp - kNetEpiWarp0) >> 2;
         uint32_t tph = 0;
         int t = 0;
         for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++t) {
@@ -371,7 +447,7 @@ net_gemm_kernel(const __grid_constant__ NetGemmParams P, const __grid_constant__
             if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) break;
             tph ^= 1u << b;
             tc_fence_after();
-            epilogue(P, tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * P.BN), mt, nt, q, lane);
+            epilogue(P, S, tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * P.BN), mt, nt, q, h, lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
