@@ -47,7 +47,8 @@ constexpr int kNetStageA = kTileM * 64;       // 8 KB: 128 rows x 32 BF16
 constexpr int kImageKBlockBytes = 2 * kNetStageA;   // split image: hi then lo per K block
 constexpr int kNetSmemLimit = 227 * 1024;
 constexpr int kNetXchFloats = 4 * kTileM;     // (max, sum, argmax, z_label) per row
-constexpr int kNetFixedSmem = 1024 + 256 + kNetXchFloats * 4;
+constexpr int kNetBiasMax = 512;               // bias staged in shared memory (N <= 512 when a bias is used)
+constexpr int kNetFixedSmem = 1024 + 256 + (kNetXchFloats + kNetBiasMax) * 4;
 
 struct NetGemmParams {
     int32_t M, N, kblocks, kb_per_split, ksplit, mtiles, ntiles;
@@ -135,9 +136,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 }
 
 // One accumulator row per thread; the warp pair of a lane quarter splits the
-// columns in halves [c_lo, c_hi).
-__device__ void epilogue(const NetGemmParams &P, const NSmem &SM, uint32_t tacc, int mt, int nt, int q, int h,
-                         int lane)
+// columns in halves [c_lo, c_hi).  bias_s: the bias in shared memory.
+template <int EPI>
+__device__ void epilogue(const NetGemmParams &P, const NSmem &SM, const float *bias_s, uint32_t tacc, int mt, int nt,
+                         int q, int h, int lane)
 {
     const int r = 32 * q + lane;
     const int64_t m = (int64_t)mt * kTileM + r;
@@ -147,7 +149,7 @@ __device__ void epilogue(const NetGemmParams &P, const NSmem &SM, uint32_t tacc,
     const int half = P.BN / 2;
     const int c_lo = h * half, c_hi = c_lo + half;
     float v[32];
-    if (P.epi == EPI_RELU || P.epi == EPI_DRELU || P.epi == EPI_ACC) {
+    if constexpr (EPI != EPI_SOFTMAX) {
         for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
             load32(tacc, c0, c_hi, v);
             if (!valid) continue;
@@ -155,12 +157,12 @@ __device__ void epilogue(const NetGemmParams &P, const NSmem &SM, uint32_t tacc,
             for (int j = 0; j < 4; ++j) {
                 const int n0 = n_base + c0 + 8 * j;
                 if (c0 + 8 * j >= c_hi || n0 >= P.N) continue;
-                float o[8];
-                if (P.epi == EPI_RELU) {
+                if constexpr (EPI == EPI_RELU) {
+                    float o[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         const int n = n0 + e;
-                        o[e] = n < P.N ? fmaxf(fmaf(v[8 * j + e], rs, P.bias ? P.bias[n] : 0.f), 0.f) : 0.f;
+                        o[e] = n < P.N ? fmaxf(fmaf(v[8 * j + e], rs, bias_s ? bias_s[n] : 0.f), 0.f) : 0.f;
                     }
                     if (n0 + 8 <= P.N) {
                         *reinterpret_cast<uint4 *>(P.out + m * P.ldo + n0) =
@@ -176,7 +178,7 @@ __device__ void epilogue(const NetGemmParams &P, const NSmem &SM, uint32_t tacc,
                         for (int e = 0; e < 8; ++e)
                             if (n0 + e < P.N) P.outT[(int64_t)(n0 + e) * P.ldt + m] = __float2bfloat16_rn(o[e]);
                     }
-                } else if (P.epi == EPI_DRELU) {
+                } else if constexpr (EPI == EPI_DRELU) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         const int n = n0 + e;
@@ -198,130 +200,144 @@ __device__ void epilogue(const NetGemmParams &P, const NSmem &SM, uint32_t tacc,
             }
         }
         return;
-    }
-    // ---------------------------------------------------------------- SOFTMAX
-    // One pass per half: running max, argmax (lowest index on ties) and the sum of
-    // exp(z - max), rescaled once per 32-column chunk; the halves then combine
-    // through shared memory.  A second pass touches only the confidence window.
-    const bool train = P.label != nullptr;
-    const int y = (train && valid) ? P.label[m] : -1;
-    float mx = -INFINITY, S = 0.f, zy = 0.f;
-    int bi = -1;
-    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
-        load32(tacc, c0, c_hi, v);
-        float cm = -INFINITY;
-        int ci = -1;
+    } else {
+        // One pass per half: running max, argmax (lowest index on ties) and the sum
+        // of exp(z - max), rescaled once per 32-column chunk; the halves then combine
+        // through shared memory.  Missing columns read as -inf (exp gives 0).
+        const bool train = P.label != nullptr;
+        const int y = (train && valid) ? P.label[m] : -1;
+        const int lim = min(c_hi, P.N);
+        float mx = -INFINITY, S = 0.f, zy = 0.f;
+        int bi = -1;
+        for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+            load32(tacc, c0, c_hi, v);
+            float cm = -INFINITY;
+            int ci = -1;
+            if (c0 + 32 <= lim) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const int n = c0 + e;
-            if (n < c_hi && n < P.N) {
-                v[e] += P.bias[n];
-                if (v[e] > cm) { cm = v[e]; ci = n; }
-                if (n == y) zy = v[e];
-                if (!train && P.outf && valid) P.outf[m * P.ldf + n] = v[e];
+                for (int e = 0; e < 32; ++e) {
+                    const float z = v[e] + bias_s[c0 + e];
+                    v[e] = z;
+                    if (z > cm) { cm = z; ci = c0 + e; }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const float z = c0 + e < lim ? v[e] + bias_s[c0 + e] : -INFINITY;
+                    v[e] = z;
+                    if (z > cm) { cm = z; ci = c0 + e; }
+                }
+            }
+            if (train) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if (c0 + e == y) zy = v[e];
+            } else if (P.outf && valid) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if (c0 + e < lim) P.outf[m * P.ldf + c0 + e] = v[e];
+            }
+            if (cm > mx) {
+                S *= __expf(mx - cm);
+                mx = cm;
+                bi = ci;
+            }
+            if (mx > -INFINITY) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) S += __expf(v[e] - mx);
             }
         }
-        if (cm > mx) {
-            S *= __expf(mx - cm);
-            mx = cm;
-            bi = ci;
+        float *X = SM.xch;   // [4][128]: max, sum, argmax, z_label
+        if (h == 1) {
+            X[r] = mx;
+            X[kTileM + r] = S;
+            X[2 * kTileM + r] = __int_as_float(bi);
+            X[3 * kTileM + r] = zy;
         }
-        if (mx > -INFINITY) {
+        pair_sync(q);
+        if (h == 0) {
+            const float m1 = X[r], s1 = X[kTileM + r], z1 = X[3 * kTileM + r];
+            const int b1 = __float_as_int(X[2 * kTileM + r]);
+            const float M = fmaxf(mx, m1);
+            const float St =
+                (mx > -INFINITY ? S * __expf(mx - M) : 0.f) + (m1 > -INFINITY ? s1 * __expf(m1 - M) : 0.f);
+            if (m1 > mx) bi = b1;
+            if (y >= c_hi) zy = z1;
+            mx = M;
+            S = St;
+            X[r] = mx;
+            X[kTileM + r] = S;
+            X[2 * kTileM + r] = __int_as_float(bi);
+        }
+        pair_sync(q);
+        if (h == 1) {
+            mx = X[r];
+            S = X[kTileM + r];
+            bi = __float_as_int(X[2 * kTileM + r]);
+        }
+        // window mass: columns within halfwin of the argmax that lie in this half.  The
+        // TMEM loads are warp-collective (.sync.aligned), so every lane walks the same
+        // 8-column groups -- those that meet any lane's window -- and masks its own.
+        float Sw = 0.f;
+        if (P.halfwin >= 0) {
+            const bool has = bi >= 0;
+            const int w0 = has ? max(c_lo, bi - P.halfwin) : c_hi;
+            const int w1 = has ? min(lim, bi + P.halfwin + 1) : c_lo;
+            int g0 = w0, g1 = w1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                g0 = min(g0, __shfl_xor_sync(0xffffffffu, g0, o));
+                g1 = max(g1, __shfl_xor_sync(0xffffffffu, g1, o));
+            }
+            for (int c0 = g0 & ~7; c0 < g1; c0 += 8) {
+                uint32_t rr[8];
+                tmem_ld8(tacc + c0, rr);
+                tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int n = c0 + e;
+                    if (n >= w0 && n < w1) Sw += __expf(__uint_as_float(rr[e]) + bias_s[n] - mx);
+                }
+            }
+        }
+        pair_sync(q);
+        if (h == 1) X[r] = Sw;
+        pair_sync(q);
+        if (h == 0) {
+            Sw += X[r];
+            if (valid) {
+                if (P.bin) P.bin[m] = max(bi, 0);
+                if (P.conf) P.conf[m] = P.halfwin >= 0 ? Sw / S : 1.0f / S;
+            }
+            if (train) {
+                float lrow = valid ? (logf(S) + mx - zy) : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) lrow += __shfl_xor_sync(0xffffffffu, lrow, o);
+                if (lane == 0 && P.loss) atomicAdd(P.loss, lrow * P.inv_batch);
+            }
+        }
+        pair_sync(q);   // the exchange buffer is reused by the next tile
+        if (!train) return;
+        const float invS = 1.0f / S;
+        for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+            load32(tacc, c0, c_hi, v);
+            if (!valid) continue;
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const int n = c0 + e;
-                if (n < c_hi && n < P.N) S += __expf(v[e] - mx);
-            }
-        }
-    }
-    float *X = SM.xch;   // [4][128]: max, sum, argmax, z_label
-    if (h == 1) {
-        X[r] = mx;
-        X[kTileM + r] = S;
-        X[2 * kTileM + r] = __int_as_float(bi);
-        X[3 * kTileM + r] = zy;
-    }
-    pair_sync(q);
-    if (h == 0) {
-        const float m1 = X[r], s1 = X[kTileM + r], z1 = X[3 * kTileM + r];
-        const int b1 = __float_as_int(X[2 * kTileM + r]);
-        const float M = fmaxf(mx, m1);
-        const float St = (mx > -INFINITY ? S * __expf(mx - M) : 0.f) + (m1 > -INFINITY ? s1 * __expf(m1 - M) : 0.f);
-        if (m1 > mx) bi = b1;
-        if (y >= c_hi) zy = z1;
-        mx = M;
-        S = St;
-        X[r] = mx;
-        X[kTileM + r] = S;
-        X[2 * kTileM + r] = __int_as_float(bi);
-    }
-    pair_sync(q);
-    if (h == 1) {
-        mx = X[r];
-        S = X[kTileM + r];
-        bi = __float_as_int(X[2 * kTileM + r]);
-    }
-    // window mass: columns within halfwin of the argmax that lie in this half.  The
-    // TMEM loads are warp-collective (.sync.aligned), so every lane walks the same
-    // 8-column groups -- those that meet any lane's window -- and masks its own.
-    float Sw = 0.f;
-    if (P.halfwin >= 0) {
-        const bool has = bi >= 0;
-        int w0 = has ? max(c_lo, bi - P.halfwin) : c_hi;
-        int w1 = has ? min(min(c_hi, P.N), bi + P.halfwin + 1) : c_lo;
-        int g0 = w0, g1 = w1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            g0 = min(g0, __shfl_xor_sync(0xffffffffu, g0, o));
-            g1 = max(g1, __shfl_xor_sync(0xffffffffu, g1, o));
-        }
-        for (int c0 = g0 & ~7; c0 < g1; c0 += 8) {
-            uint32_t rr[8];
-            tmem_ld8(tacc + c0, rr);
-            tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int n = c0 + e;
-                if (n >= w0 && n < w1) Sw += __expf(__uint_as_float(rr[e]) + P.bias[n] - mx);
-            }
-        }
-    }
-    pair_sync(q);
-    if (h == 1) X[r] = Sw;
-    pair_sync(q);
-    if (h == 0) {
-        Sw += X[r];
-        if (valid) {
-            if (P.bin) P.bin[m] = max(bi, 0);
-            if (P.conf) P.conf[m] = P.halfwin >= 0 ? Sw / S : 1.0f / S;
-        }
-        if (train) {
-            float lrow = valid ? (logf(S) + mx - zy) : 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lrow += __shfl_xor_sync(0xffffffffu, lrow, o);
-            if (lane == 0 && P.loss) atomicAdd(P.loss, lrow * P.inv_batch);
-        }
-    }
-    pair_sync(q);   // the exchange buffer is reused by the next tile
-    if (!train) return;
-    const float invS = 1.0f / S;
-    for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
-        load32(tacc, c0, c_hi, v);
-        if (!valid) continue;
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const int n = c0 + e;
-            if (n < c_hi && n < P.N) {
-                const float z = v[e] + P.bias[n];
-                const float d = (__expf(z - mx) * invS - (n == y ? 1.f : 0.f)) * P.inv_batch;
-                P.out[m * P.ldo + n] = __float2bfloat16_rn(d);
-                P.outT[(int64_t)n * P.ldt + m] = __float2bfloat16_rn(d);
-                P.outf[m * P.ldf + n] = d;
+                if (n < lim) {
+                    const float z = v[e] + bias_s[n];
+                    const float d = (__expf(z - mx) * invS - (n == y ? 1.f : 0.f)) * P.inv_batch;
+                    P.out[m * P.ldo + n] = __float2bfloat16_rn(d);
+                    P.outT[(int64_t)n * P.ldt + m] = __float2bfloat16_rn(d);
+                    P.outf[m * P.ldf + n] = d;
+                }
             }
         }
     }
 }
 
+template <int EPI>
 __global__ void __launch_bounds__(kNetThreads, 1)
 net_gemm_kernel(const __grid_constant__ NetGemmParams P, const __grid_constant__ CUtensorMap tmA,
                 const __grid_constant__ CUtensorMap tmB)
@@ -348,6 +364,11 @@ net_gemm_kernel(const __grid_constant__ NetGemmParams P, const __grid_constant__
     if (warp == 1) {
         __syncwarp();
         tmem_alloc(smem_u32(S.tmem_slot), kNetTmemCols);
+    }
+    float *bias_s = nullptr;
+    if (P.bias && P.N <= kNetBiasMax) {
+        bias_s = S.xch + kNetXchFloats;
+        for (int i = threadIdx.x; i < P.N; i += blockDim.x) bias_s[i] = P.bias[i];
     }
     tc_fence_before();
     __syncthreads();
@@ -447,7 +468,8 @@ net_gemm_kernel(const __grid_constant__ NetGemmParams P, const __grid_constant__
             if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) break;
             tph ^= 1u << b;
             tc_fence_after();
-            epilogue(P, S, tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * P.BN), mt, nt, q, h, lane);
+            epilogue<EPI>(P, S, bias_s, tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * P.BN), mt, nt, q, h,
+                          lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
@@ -652,11 +674,15 @@ cudaError_t net_gemm(const rms_plan_s &p, const NetGemm &g, cudaStream_t s)
         return cudaErrorInvalidValue;
     }
     const size_t smem = kNetFixedSmem + (size_t)P.stages * (stage + 16);
-    cudaError_t e = cudaFuncSetAttribute(net_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (g.bias && g.N > kNetBiasMax) return cudaErrorInvalidValue;
     const int64_t items = (int64_t)P.mtiles * P.ntiles * P.ksplit;
     const int grid = (int)std::min<int64_t>(items, p.num_sms);
-    net_gemm_kernel<<<grid, kNetThreads, smem, s>>>(P, tmA, tmB);
+    auto kern = g.epi == EPI_RELU ? net_gemm_kernel<EPI_RELU>
+              : g.epi == EPI_SOFTMAX ? net_gemm_kernel<EPI_SOFTMAX>
+              : g.epi == EPI_DRELU ? net_gemm_kernel<EPI_DRELU> : net_gemm_kernel<EPI_ACC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kNetThreads, smem, s>>>(P, tmA, tmB);
     return cudaGetLastError();
 }
 
