@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-paths", action="store_true", help="skip timing the other precision paths")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--nlos", type=int, default=None, help="override the workload's LOS count (profiling runs)")
     ap.add_argument("--n-train", type=int, default=1 << 20, help="learned workload: training LOS")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
     ap.add_argument("--hidden", type=int, default=256, help="learned workload: hidden units")
@@ -116,9 +117,12 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(cfg_name):
+def make_inputs(cfg_name, nlos=None):
+    import dataclasses
     from paper_1810_06250_gb300 import inputs
     cfg = inputs.CONFIGS[cfg_name]
+    if nlos is not None:
+        cfg = dataclasses.replace(cfg, nlos=nlos)
     freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
     Q, U = inputs.make_cube(cfg)
     return inputs, cfg, freq, w, phi, Q, U
@@ -159,7 +163,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    _, cfg, freq, w, phi, Q, U = make_inputs(args.config)
+    _, cfg, freq, w, phi, Q, U = make_inputs(args.config, args.nlos)
     import oracle
     oracle.build()
     op = oracle.plan(freq, "freq", w)
@@ -244,7 +248,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rms.build()
-    inputs, cfg, freq, w, phi, Q, U = make_inputs(args.config)
+    inputs, cfg, freq, w, phi, Q, U = make_inputs(args.config, args.nlos)
     nact = int(np.count_nonzero(w))
     L = cfg.nlos
     from paper_1810_06250_gb300.inputs import to_layout
@@ -268,10 +272,19 @@ def run_ours(args):
     def step():
         plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
 
+    tensor_path = args.path in ("bf16", "bf16x3", "fp16x3")
     with torch.cuda.stream(stream):
         with ClockSampler(local) as clk:
-            total_ms, per = time_steps(step, stream, args.steps, args.warmup, torch, barrier)
+            for _ in range(args.warmup):
+                step()
+            # the library records events around its two kernels on this stream
+            if tensor_path:
+                rms.rms_plan_set_kernel_timing(plan.handle, True)
+            total_ms, per = time_steps(step, stream, args.steps, 0, torch, barrier)
+            if tensor_path:
+                rms.rms_plan_set_kernel_timing(plan.handle, False)
     plan.sync(stream)
+    kt = rms.rms_plan_kernel_times(plan.handle) if tensor_path else (0.0, 0.0, 0)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         import torch.distributed as dist
@@ -286,7 +299,6 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    tensor_path = args.path in ("bf16", "bf16x3", "fp16x3")
     useful_flops = 8.0 * units
     terms = 1 if args.path == "bf16" else 3
     hbm_bytes = L * (8.0 * (nact if args.layout == "chan" else cfg.nchan) + 8.0 * cfg.nphi + 12.0)
@@ -294,14 +306,23 @@ def run_ours(args):
         peak = peaks.get("bf16_tflops_sustained")
         src = "measured sustained bf16 (MEASURED_PEAKS.json)" if peak else "fallback 1700 TFLOP/s sustained"
         peak = peak or 1700.0
-        achieved = useful_flops / (avg_launch_ms * 1e-3) / 1e12
-        traffic = measured_traffic("umma.cu", "umma_synth_lofar_bf16x3.md") \
-            if (args.path == "bf16x3" and args.layout == "chan" and args.config == CONFIG_NAME) else None
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        split_ms, gemm_ms, ncalls = kt
+        gemm_launch_ms = gemm_ms / max(1, ncalls)
+        achieved = useful_flops / (gemm_launch_ms * 1e-3) / 1e12
+        traffic = measured_traffic("gemm.cu", "gemm_lofar_bf16x3.md") \
+            if (args.path == "bf16x3" and args.layout == "chan" and args.config == CONFIG_NAME and args.nlos is None) \
+            else None
+        roof = {"kernel": "gemm_kernel (tensor-core contraction)", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)", "peak_source": src,
+                "launch_ms": gemm_launch_ms, "split_launch_ms": split_ms / max(1, ncalls),
+                "timed_launches": ncalls,
                 "issued_tflops": achieved * terms, "issued_frac": achieved * terms / peak,
-                "hbm_gbs": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9,
-                "algorithmic": "8 flop per (LOS, active channel, phi); %d tensor products issued per flop" % terms}
+                "step_frac": useful_flops / (avg_launch_ms * 1e-3) / 1e12 / peak,
+                "hbm_gbs_step": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9,
+                "algorithmic": "8 flop per (LOS, active channel, phi) (complex MAC); %d tensor products issued "
+                               "per flop; achieved = algorithmic flop per launch / the contraction kernel's "
+                               "CUDA-event duration" % terms}
     else:
         props = torch.cuda.get_device_properties(dev)
         clk_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -322,7 +343,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (0.84 GB in, 0.84 GB out per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "units_per_step_total_channels": L * cfg.nchan * cfg.nphi},
-            "roofline": roof, "gpu_launches": args.steps * (2 if args.path == "fp16x3" else 1),
+            "roofline": roof, "gpu_launches": args.steps * (2 if tensor_path else 1),
             "plan_ms": plan_ms, "clocks": clk.summary()}
 
     if rank == 0 and world == 1 and not args.no_paths:
@@ -412,6 +433,9 @@ def run_learned(args):
     dev = torch.device("cuda", local)
     rms.build()
     cfg = inputs.CONFIGS["learned"]
+    if args.nlos is not None:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, nlos=args.nlos)
     freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
     nact = int(np.count_nonzero(w))
     L = cfg.nlos

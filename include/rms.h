@@ -216,6 +216,19 @@ const char *rms_status_string(rms_status s);
  * RMS_ERR_TIMEOUT on the plan and returns. */
 rms_status rms_plan_set_timeout(rms_plan_t plan, int64_t ns);
 
+/*
+ * Kernel timing for measurement (the paper has no counterpart).  While enabled,
+ * every tensor-core synthesis call on the plan records CUDA events on its
+ * stream around its two kernels (the layout stage that splits the cube into
+ * 16-bit operands, and the tensor-core contraction).  rms_plan_kernel_times
+ * waits for the recorded events, returns the summed milliseconds of each kernel
+ * and the number of calls timed (host outputs, each may be NULL), and forgets
+ * them.  FP32 plans and calls made while disabled record nothing.  Timing adds
+ * three event records per call; it is off by default.
+ */
+rms_status rms_plan_set_kernel_timing(rms_plan_t plan, int32_t enable);
+rms_status rms_plan_kernel_times(rms_plan_t plan, double *split_ms, double *contract_ms, int64_t *calls);
+
 /* ==========================================================================
  * Synthetic sources on the device (Sec. 2.1 source models)
  * ========================================================================== */

@@ -34,7 +34,8 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_plan_sync", "rms_plan_info", "rms_plan_get", "rms_plan_destroy", "rms_status_string",
            "rms_plan_set_timeout", "rms_generate", "rms_net_create", "rms_net_destroy", "rms_net_info",
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
-           "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned")
+           "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
+           "rms_plan_kernel_times")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -82,6 +83,8 @@ def load(path: str = LIB_PATH):
             "rms_plan_destroy": [P],
             "rms_plan_set_timeout": [P, _i64],
             "rms_generate": [P, P, _i64, _i64, _i32, P, P, P],
+            "rms_plan_set_kernel_timing": [P, _i32],
+            "rms_plan_kernel_times": [P, P, P, P],
             "rms_net_create": [ctypes.POINTER(P), P, _i32, _i32, ctypes.c_uint64],
             "rms_net_destroy": [P],
             "rms_net_info": [P, _i32, P],
@@ -346,3 +349,15 @@ def rms_peakmap_learned(win: int, net: int, Q, U, nlos: int, layout, tau: float,
                                     _dptr(fallback, torch.int32, "fallback"),
                                     _dptr(nfallback, torch.int64, "nfallback"), _stream(stream))
     _check(st, "rms_peakmap_learned")
+
+
+def rms_plan_set_kernel_timing(plan: int, enable: bool):
+    _check(load().rms_plan_set_kernel_timing(plan, 1 if enable else 0), "rms_plan_set_kernel_timing")
+
+
+def rms_plan_kernel_times(plan: int):
+    """(split_ms, contraction_ms, calls) summed over the calls timed since the last read."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), _i64()
+    _check(load().rms_plan_kernel_times(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
+           "rms_plan_kernel_times")
+    return a.value, b.value, n.value

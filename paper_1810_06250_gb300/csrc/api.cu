@@ -69,6 +69,7 @@ void free_plan(rms_plan_s *p)
     cudaFree(p->d_stage);
     cudaFree(p->d_rexp);
     cudaFree(p->d_scratch);
+    for (cudaEvent_t x : p->tev) cudaEventDestroy(x);
     if (p->last) cudaEventDestroy(p->last);
     if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
@@ -429,8 +430,25 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
             cudaGetLastError();
             return from_cuda(e);
         }
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        if (p->timing) {
+            for (auto &x : ev)
+                if (cudaEventCreate(&x) != cudaSuccess) x = nullptr;
+            if (ev[0] && ev[1] && ev[2]) {
+                cudaEventRecord(ev[0], s);
+            } else {
+                for (auto &x : ev)
+                    if (x) cudaEventDestroy(x);
+                ev[0] = ev[1] = ev[2] = nullptr;
+            }
+            cudaGetLastError();
+        }
         e = launch_split_gemm(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, scr,
-                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s);
+                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s, ev[1]);
+        if (ev[2]) {
+            if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
+            p->tev.insert(p->tev.end(), ev, ev + 3);
+        }
         cudaError_t e2 = cudaFreeAsync(scr, s);
         if (e == cudaSuccess) e = e2;
         break;
@@ -524,6 +542,37 @@ rms_status rms_plan_sync(rms_plan_t p, void *stream)
     *p->h_err = 0;
     if (e != cudaSuccess) return RMS_ERR_CUDA;
     return err ? RMS_ERR_TIMEOUT : RMS_OK;
+}
+
+rms_status rms_plan_set_kernel_timing(rms_plan_t p, int32_t enable)
+{
+    if (!p) return RMS_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    return RMS_OK;
+}
+
+rms_status rms_plan_kernel_times(rms_plan_t p, double *split_ms, double *contract_ms, int64_t *calls)
+{
+    if (!p) return RMS_ERR_INVALID_ARG;
+    DeviceGuard guard(p->device);
+    double a = 0.0, b = 0.0;
+    int64_t n = 0;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i + 2 < p->tev.size(); i += 3) {
+        float t0 = 0.f, t1 = 0.f;
+        if (e == cudaSuccess) e = cudaEventSynchronize(p->tev[i + 2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, p->tev[i], p->tev[i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, p->tev[i + 1], p->tev[i + 2]);
+        a += t0;
+        b += t1;
+        ++n;
+    }
+    for (cudaEvent_t x : p->tev) cudaEventDestroy(x);
+    p->tev.clear();
+    if (split_ms) *split_ms = a;
+    if (contract_ms) *contract_ms = b;
+    if (calls) *calls = n;
+    return from_cuda(e);
 }
 
 rms_status rms_plan_set_timeout(rms_plan_t p, int64_t ns)

@@ -754,7 +754,7 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
 
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
-                              cudaStream_t s)
+                              cudaStream_t s, cudaEvent_t ev_mid)
 {
     SplitOpts so;
     so.Q = Q;
@@ -766,6 +766,7 @@ cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *
     so.rexp = rexp;
     cudaError_t e = launch_split(p, so, s);
     if (e != cudaSuccess) return e;
+    if (ev_mid && (e = cudaEventRecord(ev_mid, s)) != cudaSuccess) return e;
     GemmOpts go;
     go.A = A;
     go.nlos = nlos;

@@ -72,6 +72,11 @@ struct rms_plan_s {
     // FP16X3: per-LOS exponent scratch
     size_t rexp_cap = 0;
     int8_t *d_rexp = nullptr;
+
+    // optional kernel timing (rms_plan_set_kernel_timing): events around the layout
+    // stage and the contraction of each tensor-core synthesis call
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;   // triples: before split, after split, after contraction
 };
 
 // phase.cu
@@ -132,7 +137,7 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
                                 const int64_t *count, int64_t nmax, uint8_t *dst, cudaStream_t s);
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
-                              cudaStream_t s);
+                              cudaStream_t s, cudaEvent_t ev_mid = nullptr);
 
 // generate.cu
 cudaError_t launch_generate(const rms_plan_s &p, const rms_source_model &m, int64_t los0, int64_t nlos,
