@@ -548,11 +548,12 @@ def run_learned(args):
         import oracle
         oracle.build()
         op = oracle.plan(freq, "freq", w)
-        Qc, Uc = inputs.make_cube(cfg, 0, 2048)
+        Qc, Uc = inputs.make_cube(cfg, 0, 128)
         t0 = time.perf_counter()
-        oracle.synth(Qc[:128], Uc[:128], op, phi)
+        oracle.synth(Qc, Uc, op, phi)
         per_los = (time.perf_counter() - t0) / 128
-        n = int(min(2048, max(128, args.cpu_seconds / per_los)))
+        n = int(min(L, max(128, args.cpu_seconds / per_los)))
+        Qc, Uc = inputs.make_cube(cfg, 0, n)
         t0 = time.perf_counter()
         oracle.peak(oracle.synth(Qc[:n], Uc[:n], op, phi))
         dt = time.perf_counter() - t0

@@ -132,10 +132,11 @@ rms_status rms_rmsf(rms_plan_t plan, float *R_out, double *lambda0sq, double *K,
  * rounded to FP32 separately, so the peak index can be recomputed bit-exactly
  * from F_out.  Asynchronous, no host sync.  The tensor-core precisions take a
  * per-call scratch from the device's default stream-ordered memory pool on
- * `stream` (cudaMallocAsync / cudaFreeAsync): the cube split into 16-bit
- * operands, 4 bytes per (LOS, contraction channel) (2 for RMS_BF16), and for
- * RMS_FP16X3 one exponent byte per LOS; creating a tensor-core plan sets that
- * pool to keep freed memory reserved.  The FP32 precisions allocate nothing.
+ * `stream` (cudaMallocAsync / cudaFreeAsync): the cube split into 16-bit hi and
+ * lo operands, 8 bytes per (LOS, contraction channel slot; the channels are
+ * padded to a multiple of 16 per 128 LOS), and for RMS_FP16X3 one exponent
+ * byte per LOS; creating a tensor-core plan sets that pool to keep freed
+ * memory reserved.  The FP32 precisions allocate nothing.
  */
 rms_status rms_synth(rms_plan_t plan, const float *Q, const float *U, int64_t nlos, int32_t layout,
                      float *F_out, int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream);
