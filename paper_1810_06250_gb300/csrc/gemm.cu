@@ -685,7 +685,17 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.count = o.count;
     P.rows = o.rows;
     P.kblocks = chan ? p.kblocks : p.kblocks_raw;
-    int ngroups = (P.kblocks + kGroupKBlocks - 1) / kGroupKBlocks;
+    // K blocks chained into one TMEM partial before the round-to-nearest fold: the
+    // tensor core's accumulation error grows ~4e-8 per chained MMA, which matters for
+    // the split precisions only; plain BF16 (error ~1e-3) folds once per N tile.
+    // RMS_GROUP_KBLOCKS (2..16) overrides the split-precision group (a tuning knob).
+    static const int group_split = [] {
+        const char *v = std::getenv("RMS_GROUP_KBLOCKS");
+        const int g = v ? std::atoi(v) : 0;
+        return (g >= 2 && g <= 16) ? g : kGroupKBlocks;
+    }();
+    const int group_max = mode == MODE_BF16 ? P.kblocks : group_split;
+    int ngroups = (P.kblocks + group_max - 1) / group_max;
     P.group = (P.kblocks + ngroups - 1) / ngroups;
     P.nphi = p.nphi;
     P.ntiles_n = p.ntiles_n;

@@ -18,7 +18,7 @@ constexpr int kChanPerKBlock = 16; // active channels per pipeline stage
 constexpr int kKBlock = 32;        // K values (Q and U interleaved) per stage = 64 bytes of bf16
 constexpr int kMaxTileN = 208;     // phase-matrix rows per tile: each of the two epilogue warps
                                    // sharing a row keeps tile_n / 2 FP32 sums in registers
-constexpr int kGroupKBlocks = 6;   // K blocks accumulated in TMEM before the FP32 register fold
+constexpr int kGroupKBlocks = 8;   // K blocks accumulated in TMEM before the FP32 register fold (split precisions)
 
 struct rms_plan_s {
     int device = 0;

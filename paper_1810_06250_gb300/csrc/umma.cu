@@ -46,6 +46,9 @@
 
 namespace {
 
+// K blocks per TMEM partial before the FP32 register fold in this kernel
+constexpr int kUmmaGroupKBlocks = 6;
+
 constexpr int kThreads = 512;
 constexpr int kConvWarp0 = 4, kNumConvWarps = 4;
 constexpr int kEpiWarp0 = 8, kNumEpiWarps = 8;
@@ -773,7 +776,7 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
     P.kbmask = p.d_kbmask;
     P.nk = chan ? p.nact : p.nchan;
     P.kblocks = chan ? p.kblocks : p.kblocks_raw;
-    int ngroups = (P.kblocks + kGroupKBlocks - 1) / kGroupKBlocks;
+    int ngroups = (P.kblocks + kUmmaGroupKBlocks - 1) / kUmmaGroupKBlocks;
     P.group = (P.kblocks + ngroups - 1) / ngroups;
     P.nphi = p.nphi;
     P.ntiles_n = p.ntiles_n;

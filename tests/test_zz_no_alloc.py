@@ -3,7 +3,9 @@
 It exists for callers that cannot allocate device memory while they process
 data (memory reserved up front, or owned by another allocator).  Its results
 must match rms_synth's on the same plan, call after call, although every call
-reuses the same fixed scratch array.  This file is collected last on purpose.
+reuses the same fixed scratch array (within the FP16X3 tolerance: the two
+kernels fold their partial sums in different groups).  This file is collected
+last on purpose.
 """
 import numpy as np
 import pytest
@@ -54,9 +56,13 @@ def test_noalloc_matches_rms_synth(rms, layout):
             Fa, Fb = F0.cpu().numpy(), F1.cpu().numpy()
             per, _ = gh.errors(Fb[..., 0] + 1j * Fb[..., 1], Fa[..., 0] + 1j * Fa[..., 1])
             assert per.max() <= gh.TOL["fp16x3"], per.max()
-            np.testing.assert_array_equal(i1.cpu().numpy(), i0.cpu().numpy())
-            np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
-            np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+            # the two kernels fold their FP32 partial sums in different groups, so F may
+            # differ in the last bits: each peak map is exact for its own F, and the two
+            # agree wherever the top-2 gap of F clears the tolerance
+            for F, i, a, p in ((Fa, i0, a0, p0), (Fb, i1, a1, p1)):
+                gh.check_peaks_self(F, i.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy(), phi)
+            gh.check_peaks_oracle(i1.cpu().numpy(), Fa[..., 0] + 1j * Fa[..., 1], gh.TOL["fp16x3"])
+            np.testing.assert_allclose(a1.cpu().numpy(), a0.cpu().numpy(), rtol=2 * gh.TOL["fp16x3"])
 
 
 def test_noalloc_limits(rms):
