@@ -285,12 +285,8 @@ def run_ours(args):
                 rms.rms_plan_set_kernel_timing(plan.handle, False)
     plan.sync(stream)
     kt = rms.rms_plan_kernel_times(plan.handle) if tensor_path else (0.0, 0.0, 0)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = world * units * args.steps / (tmax * 1e-3) / 1e9
+    from paper_1810_06250_gb300.dist import throughput
+    value, tmax = throughput(units, args.steps, total_ms, world, dev)
     avg_launch_ms = statistics.mean(per)
 
     # roofline of the dominant kernel (the synthesis kernel: one launch per step)
@@ -485,12 +481,8 @@ def run_learned(args):
     ms_bf16 = t_bf16 / max(3, args.steps // 2)
     agree = float(np.mean(np.abs(php.cpu().numpy().astype(np.float64) - fphi.cpu().numpy()) <= 0.5 * (1 + 1e-6)))
     fbr = float(fb.cpu().numpy().mean())
-    t = torch.tensor([t_learn], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = world * units * args.steps / (tmax * 1e-3) / 1e9
+    from paper_1810_06250_gb300.dist import throughput
+    value, tmax = throughput(units, args.steps, t_learn, world, dev)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -279,3 +279,24 @@ def test_large_full(rms, inputs, oracle_mod, cfg_name, path, nsample):
         assert ok, info
     del F, q, u
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------- kernel timing hook
+def test_kernel_timing_hook(rms, inputs):
+    cfg = inputs.CONFIGS["tiny"]
+    freq, w, phi = axes(inputs, cfg)
+    Q, U = inputs.make_cube(cfg)
+    dev = torch.device("cuda")
+    q = torch.from_numpy(inputs.to_layout(Q, "chan")).to(dev)
+    u = torch.from_numpy(inputs.to_layout(U, "chan")).to(dev)
+    pidx = torch.empty(cfg.nlos, dtype=torch.int32, device=dev)
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        plan.synth(q, u, cfg.nlos, "chan", None, pidx)            # timing off: nothing recorded
+        rms.rms_plan_set_kernel_timing(plan.handle, True)
+        for _ in range(3):
+            plan.synth(q, u, cfg.nlos, "chan", None, pidx)
+        rms.rms_plan_set_kernel_timing(plan.handle, False)
+        plan.synth(q, u, cfg.nlos, "chan", None, pidx)
+        a, b, n = rms.rms_plan_kernel_times(plan.handle)
+        assert n == 3 and a > 0 and b > 0
+        assert rms.rms_plan_kernel_times(plan.handle)[2] == 0     # read once, then forgotten
