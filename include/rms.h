@@ -144,9 +144,15 @@ rms_status rms_synth(rms_plan_t plan, const float *Q, const float *U, int64_t nl
 /*
  * rms_synth from HOST buffers: copies Q and U to the device, synthesises, copies
  * F and the peak map back, and synchronises.  Same arguments as rms_synth with
- * every array a host pointer (pinned memory gives full copy bandwidth).  The
- * plan keeps device staging buffers between calls (grown on demand, freed by
- * rms_plan_destroy).  Returns RMS_ERR_OOM when staging cannot be allocated.
+ * every array a host pointer.  Large cubes are processed in chunks of LOS
+ * (LOS-major: max(16384, nlos / 16); channel-major: max(65536, nlos / 4),
+ * whose 2-D copies need long rows) through three device slots, with the
+ * copies in on a plan-owned stream, the synthesis on `stream` and the copies
+ * out on a second plan-owned stream, so that they overlap; a channel-major
+ * chunk is copied as a 2-D sub-array.  The copies overlap only from pinned
+ * (page-locked) host memory.  The plan keeps the device slots between calls
+ * (grown on demand, freed by rms_plan_destroy).  Returns RMS_ERR_OOM when they
+ * cannot be allocated.
  */
 rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64_t nlos,
                           int32_t layout, float *F_out, int32_t *peak_idx, float *peak_abs,

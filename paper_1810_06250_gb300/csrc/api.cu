@@ -70,6 +70,10 @@ void free_plan(rms_plan_s *p)
     cudaFree(p->d_rexp);
     cudaFree(p->d_scratch);
     for (cudaEvent_t x : p->tev) cudaEventDestroy(x);
+    for (cudaEvent_t x : p->hev)
+        if (x) cudaEventDestroy(x);
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
     if (p->last) cudaEventDestroy(p->last);
     if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
@@ -493,11 +497,30 @@ rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t 
     DeviceGuard guard(p->device);
     if (!guard.ok) return RMS_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t in_b = (size_t)nlos * p->nchan * sizeof(float);
-    const size_t f_b = F_out ? (size_t)nlos * p->nphi * 2 * sizeof(float) : 0;
-    const size_t pk_b = (size_t)nlos * sizeof(float);
+    // Chunks of LOS flow through kSlots device slots: copy in (stream h2d), synthesis
+    // (the caller's stream), copy out (stream d2h), so the three overlap.  A cube of
+    // fewer than two chunks runs as one chunk.
+    constexpr int kSlots = 3;
+    // Chunk sizes measured on GB300 (LOFAR cube, pinned memory): LOS-major chunks are
+    // contiguous, and 16 of them pipeline best; a channel-major chunk is a 2-D copy of
+    // one row per channel, efficient only when rows are >= 256 KB (65536 LOS).
+    // RMS_HOST_CHUNK (LOS, >= 1024) overrides the chunk size (a tuning knob).
+    static const int64_t knob = [] {
+        const char *v = std::getenv("RMS_HOST_CHUNK");
+        const long long c = v ? std::atoll(v) : 0;
+        return c >= 1024 ? (int64_t)c : (int64_t)0;
+    }();
+    const int64_t chunk = knob ? knob
+                               : layout == RMS_LOS_MAJOR ? std::max<int64_t>(16384, (nlos + 15) / 16)
+                                                         : std::max<int64_t>(65536, (nlos + 3) / 4);
+    const int64_t nchunks = (nlos + chunk - 1) / chunk;
+    const int slots = (int)std::min<int64_t>(kSlots, nchunks);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t need = 2 * up(in_b) + up(f_b) + 3 * up(pk_b);
+    const size_t in_b = (size_t)chunk * p->nchan * sizeof(float);
+    const size_t f_b = F_out ? (size_t)chunk * p->nphi * 2 * sizeof(float) : 0;
+    const size_t pk_b = (size_t)chunk * sizeof(float);
+    const size_t slot_bytes = 2 * up(in_b) + up(f_b) + 3 * up(pk_b);
+    const size_t need = slots * slot_bytes;
     if (need > p->stage_bytes) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return from_cuda(e);
@@ -510,24 +533,66 @@ rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t 
         }
         p->stage_bytes = need;
     }
-    char *b = static_cast<char *>(p->d_stage);
-    float *dQ = reinterpret_cast<float *>(b);
-    float *dU = reinterpret_cast<float *>(b + up(in_b));
-    float *dF = F_out ? reinterpret_cast<float *>(b + 2 * up(in_b)) : nullptr;
-    char *pk = b + 2 * up(in_b) + up(f_b);
-    int32_t *dI = peak_idx ? reinterpret_cast<int32_t *>(pk) : nullptr;
-    float *dA = peak_abs ? reinterpret_cast<float *>(pk + up(pk_b)) : nullptr;
-    float *dP = phi_peak ? reinterpret_cast<float *>(pk + 2 * up(pk_b)) : nullptr;
-    cudaError_t e = cudaMemcpyAsync(dQ, Q, in_b, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dU, U, in_b, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return from_cuda(e);
-    st = synth_device(p, dQ, dU, nlos, layout, dF, dI, dA, dP, s);
+    if (!p->s_h2d && cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking) != cudaSuccess) return RMS_ERR_CUDA;
+    if (!p->s_d2h && cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking) != cudaSuccess) return RMS_ERR_CUDA;
+    for (int k = 0; k < 3 * kSlots; ++k)
+        if (!p->hev[k] && cudaEventCreateWithFlags(&p->hev[k], cudaEventDisableTiming) != cudaSuccess)
+            return RMS_ERR_CUDA;
+    cudaEvent_t *ev_in = p->hev, *ev_syn = p->hev + kSlots, *ev_out = p->hev + 2 * kSlots;
+    // the staging slots may still be read by an earlier call's copies: start after them
+    cudaError_t e = cudaStreamSynchronize(p->s_d2h);
+    for (int64_t i = 0; i < nchunks && e == cudaSuccess && st == RMS_OK; ++i) {
+        const int k = (int)(i % slots);
+        const int64_t r0 = i * chunk, n = std::min(chunk, nlos - r0);
+        char *b = static_cast<char *>(p->d_stage) + k * slot_bytes;
+        float *dQ = reinterpret_cast<float *>(b);
+        float *dU = reinterpret_cast<float *>(b + up(in_b));
+        float *dF = F_out ? reinterpret_cast<float *>(b + 2 * up(in_b)) : nullptr;
+        char *pk = b + 2 * up(in_b) + up(f_b);
+        int32_t *dI = peak_idx ? reinterpret_cast<int32_t *>(pk) : nullptr;
+        float *dA = peak_abs ? reinterpret_cast<float *>(pk + up(pk_b)) : nullptr;
+        float *dP = phi_peak ? reinterpret_cast<float *>(pk + 2 * up(pk_b)) : nullptr;
+        // copy in, once this slot's previous copy-out has finished
+        if (i >= slots) e = cudaStreamWaitEvent(p->s_h2d, ev_out[k], 0);
+        if (e != cudaSuccess) break;
+        if (layout == RMS_LOS_MAJOR) {
+            e = cudaMemcpyAsync(dQ, Q + r0 * p->nchan, (size_t)n * p->nchan * sizeof(float), cudaMemcpyHostToDevice,
+                                p->s_h2d);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dU, U + r0 * p->nchan, (size_t)n * p->nchan * sizeof(float),
+                                    cudaMemcpyHostToDevice, p->s_h2d);
+        } else {   // channel-major: the chunk is n columns of every channel row
+            e = cudaMemcpy2DAsync(dQ, n * sizeof(float), Q + r0, nlos * sizeof(float), n * sizeof(float), p->nchan,
+                                  cudaMemcpyHostToDevice, p->s_h2d);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(dU, n * sizeof(float), U + r0, nlos * sizeof(float), n * sizeof(float),
+                                      p->nchan, cudaMemcpyHostToDevice, p->s_h2d);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], p->s_h2d);
+        // synthesis on the caller's stream
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_in[k], 0);
+        if (e != cudaSuccess) break;
+        st = synth_device(p, dQ, dU, n, layout, dF, dI, dA, dP, s);
+        if (st != RMS_OK) break;
+        e = cudaEventRecord(ev_syn[k], s);
+        // copy out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, ev_syn[k], 0);
+        if (e == cudaSuccess && F_out)
+            e = cudaMemcpyAsync(F_out + r0 * p->nphi * 2, dF, (size_t)n * p->nphi * 2 * sizeof(float),
+                                cudaMemcpyDeviceToHost, p->s_d2h);
+        if (e == cudaSuccess && dI)
+            e = cudaMemcpyAsync(peak_idx + r0, dI, n * sizeof(int32_t), cudaMemcpyDeviceToHost, p->s_d2h);
+        if (e == cudaSuccess && dA)
+            e = cudaMemcpyAsync(peak_abs + r0, dA, n * sizeof(float), cudaMemcpyDeviceToHost, p->s_d2h);
+        if (e == cudaSuccess && dP)
+            e = cudaMemcpyAsync(phi_peak + r0, dP, n * sizeof(float), cudaMemcpyDeviceToHost, p->s_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_out[k], p->s_d2h);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(p->s_d2h);
+    if (e == cudaSuccess) e = e2;
+    e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
     if (st != RMS_OK) return st;
-    if (F_out) e = cudaMemcpyAsync(F_out, dF, f_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && dI) e = cudaMemcpyAsync(peak_idx, dI, pk_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && dA) e = cudaMemcpyAsync(peak_abs, dA, pk_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && dP) e = cudaMemcpyAsync(phi_peak, dP, pk_b, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
     return *p->h_err ? RMS_ERR_TIMEOUT : RMS_OK;
 }

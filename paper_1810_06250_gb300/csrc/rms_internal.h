@@ -59,9 +59,11 @@ struct rms_plan_s {
     int64_t timeout_ns = 2000000000LL;
     int num_sms = 0;
 
-    // rms_synth_host staging
+    // rms_synth_host staging: slots of LOS chunks, copy streams and their events
     size_t stage_bytes = 0;
     void *d_stage = nullptr;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t hev[9] = {};
 
     // tensor paths: per-CTA split-A scratch, [num_sms][max kblocks][128][128 B]
     void *d_scratch = nullptr;

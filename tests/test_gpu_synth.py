@@ -300,3 +300,35 @@ def test_kernel_timing_hook(rms, inputs):
         a, b, n = rms.rms_plan_kernel_times(plan.handle)
         assert n == 3 and a > 0 and b > 0
         assert rms.rms_plan_kernel_times(plan.handle)[2] == 0     # read once, then forgotten
+
+
+# ------------------------------------------------------------------- host-buffer entry point
+@pytest.mark.parametrize("layout", ["chan", "los"])
+def test_synth_host_matches_device(rms, inputs, layout):
+    """rms_synth_host pipelines LOS chunks (copy in / synthesis / copy out on three
+    streams); every LOS is its own contraction, so its results equal rms_synth's
+    bit for bit, across chunk boundaries, slot reuse and a ragged last chunk."""
+    from paper_1810_06250_gb300 import learned as L
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = axes(inputs, cfg)
+    n = 140000                                   # LOS-major: 9 chunks of 16384; channel-major: 3 of 65536
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        q, u = L.generate(plan.handle, cfg, 0, n, layout)
+        F0 = torch.empty(n, cfg.nphi, 2, device="cuda")
+        i0 = torch.empty(n, dtype=torch.int32, device="cuda")
+        a0 = torch.empty(n, device="cuda")
+        p0 = torch.empty(n, device="cuda")
+        plan.synth(q, u, n, layout, F0, i0, a0, p0)
+        plan.sync()
+        qh, uh = q.cpu().pin_memory(), u.cpu().pin_memory()
+        F1 = torch.full((n, cfg.nphi, 2), float("nan")).pin_memory()
+        i1 = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+        a1 = torch.zeros(n).pin_memory()
+        p1 = torch.zeros(n).pin_memory()
+        for _ in range(2):                       # twice: the slots are reused across calls
+            plan.synth_host(qh, uh, n, layout, F1, i1, a1, p1)
+        assert torch.equal(F1, F0.cpu())
+        assert torch.equal(i1, i0.cpu()) and torch.equal(a1, a0.cpu()) and torch.equal(p1, p0.cpu())
+        i2 = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+        plan.synth_host(qh, uh, n, layout, None, i2)           # peak map only
+        assert torch.equal(i2, i0.cpu())
