@@ -142,6 +142,28 @@ rms_status rms_synth(rms_plan_t plan, const float *Q, const float *U, int64_t nl
                      float *F_out, int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream);
 
 /*
+ * rms_synth with the paper's full set of peak outputs (Sec. 2.2: the values of
+ * Q~ and U~ where |F~| peaks, and the polarisation angle there).  Arguments as
+ * rms_synth; the peak outputs come in a struct, every pointer a device [nlos]
+ * array or NULL:
+ *   peak_idx, peak_abs, phi_peak  as rms_synth;
+ *   q_peak, u_peak  Re F and Im F (K-scaled, Eqs. qPhi, uPhi) at peak_idx;
+ *   chi0            0.5 atan2(u_peak, q_peak) - phi_peak lambda_0^2 reduced to
+ *                   [0, pi): the angle of the Sec. 2.2 relation (printed garbled
+ *                   there; for a Faraday-thin source on the grid it is the
+ *                   source's intrinsic chi0).  NaN where peak_idx = -1.
+ * q_peak, u_peak and chi0 need a tensor-core precision (RMS_ERR_UNSUPPORTED for
+ * the FP32 precisions).  RMS_ERR_INVALID_ARG for a NULL `out`.
+ */
+typedef struct {
+    int32_t *peak_idx;
+    float *peak_abs, *phi_peak;
+    float *q_peak, *u_peak, *chi0;
+} rms_peak_outputs;
+rms_status rms_synth_peaks(rms_plan_t plan, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                           float *F_out, const rms_peak_outputs *out, void *stream);
+
+/*
  * rms_synth from HOST buffers: copies Q and U to the device, synthesises, copies
  * F and the peak map back, and synchronises.  Same arguments as rms_synth with
  * every array a host pointer.  Large cubes are processed in chunks of LOS

@@ -214,3 +214,14 @@ def fwhm_measured(p: Plan) -> float:
         else:
             hi = mid
     return 2.0 * 0.5 * (lo + hi)
+
+
+def chi0(F_peak, phi_peak, lambda0sq):
+    """Polarisation angle at the peak (Sec. 2.2): 0.5 arg F(phi_peak) - phi_peak lambda_0^2, in [0, pi).
+
+    The printed relation is garbled (an angle times a complex factor); this is its
+    reading from the thin-source identity F(phi0) = p0 exp(2i (chi0 + phi0 lambda_0^2)).
+    """
+    F_peak = np.asarray(F_peak)
+    x = 0.5 * np.arctan2(F_peak.imag, F_peak.real) - np.asarray(phi_peak, dtype=np.float64) * lambda0sq
+    return x - np.pi * np.floor(x / np.pi)

@@ -35,9 +35,15 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_plan_set_timeout", "rms_generate", "rms_net_create", "rms_net_destroy", "rms_net_info",
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
-           "rms_plan_kernel_times")
+           "rms_plan_kernel_times", "rms_synth_peaks")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
+
+
+class rms_peak_outputs(ctypes.Structure):
+    """Mirror of the C struct rms_peak_outputs (include/rms.h)."""
+    _fields_ = [("peak_idx", ctypes.c_void_p), ("peak_abs", ctypes.c_void_p), ("phi_peak", ctypes.c_void_p),
+                ("q_peak", ctypes.c_void_p), ("u_peak", ctypes.c_void_p), ("chi0", ctypes.c_void_p)]
 
 
 class rms_source_model(ctypes.Structure):
@@ -84,6 +90,7 @@ def load(path: str = LIB_PATH):
             "rms_plan_set_timeout": [P, _i64],
             "rms_generate": [P, P, _i64, _i64, _i32, P, P, P],
             "rms_plan_set_kernel_timing": [P, _i32],
+            "rms_synth_peaks": [P, P, P, _i64, _i32, P, P, P],
             "rms_plan_kernel_times": [P, P, P, P],
             "rms_net_create": [ctypes.POINTER(P), P, _i32, _i32, ctypes.c_uint64],
             "rms_net_destroy": [P],
@@ -361,3 +368,15 @@ def rms_plan_kernel_times(plan: int):
     _check(load().rms_plan_kernel_times(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)),
            "rms_plan_kernel_times")
     return a.value, b.value, n.value
+
+
+def rms_synth_peaks(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None, peak_abs=None, phi_peak=None,
+                    q_peak=None, u_peak=None, chi0=None, stream=None):
+    """rms_synth with Q, U at the peak and the angle chi0 there (include/rms.h)."""
+    import torch
+    out = rms_peak_outputs(_dptr(peak_idx, torch.int32, "peak_idx"), _dptr(peak_abs, torch.float32, "peak_abs"),
+                           _dptr(phi_peak, torch.float32, "phi_peak"), _dptr(q_peak, torch.float32, "q_peak"),
+                           _dptr(u_peak, torch.float32, "u_peak"), _dptr(chi0, torch.float32, "chi0"))
+    st = load().rms_synth_peaks(plan, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
+                                _layout(layout), _dptr(F_out, None, "F_out"), ctypes.byref(out), _stream(stream))
+    _check(st, "rms_synth_peaks")

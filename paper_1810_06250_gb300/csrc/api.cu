@@ -398,23 +398,31 @@ rms_status rms_rmsf(rms_plan_t p, float *R_out, double *lambda0sq, double *K, do
     return RMS_OK;
 }
 
+// Optional peak outputs beyond index, |F| and phi (tensor-core precisions only).
+struct PeakExtras {
+    float *q = nullptr, *u = nullptr, *chi = nullptr;
+};
+
 static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
-                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s);
+                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s,
+                               const PeakExtras &x);
 
 static rms_status synth_device(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
-                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s)
+                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s,
+                               const PeakExtras &x = PeakExtras())
 {
     // the plan's scratch is shared by its calls: order them on the device
     cudaError_t e = cudaStreamWaitEvent(s, p->last, 0);
     if (e != cudaSuccess) return from_cuda(e);
-    rms_status st = synth_launch(p, Q, U, nlos, layout, F, pidx, pabs, pphi, s);
+    rms_status st = synth_launch(p, Q, U, nlos, layout, F, pidx, pabs, pphi, s, x);
     e = cudaEventRecord(p->last, s);
     if (st == RMS_OK && e != cudaSuccess) st = from_cuda(e);
     return st;
 }
 
 static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
-                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s)
+                               float *F, int32_t *pidx, float *pabs, float *pphi, cudaStream_t s,
+                               const PeakExtras &x)
 {
     cudaError_t e = cudaSuccess;
     switch (p->precision) {
@@ -448,7 +456,7 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
             cudaGetLastError();
         }
         e = launch_split_gemm(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, scr,
-                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s, ev[1]);
+                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s, ev[1], x.q, x.u, x.chi);
         if (ev[2]) {
             if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
             p->tev.insert(p->tev.end(), ev, ev + 3);
@@ -485,6 +493,27 @@ rms_status rms_synth(rms_plan_t p, const float *Q, const float *U, int64_t nlos,
     if (!guard.ok) return RMS_ERR_CUDA;
     return synth_device(p, Q, U, nlos, layout, F_out, peak_idx, peak_abs, phi_peak,
                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+rms_status rms_synth_peaks(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout, float *F_out,
+                           const rms_peak_outputs *out, void *stream)
+{
+    rms_status st = check_synth_args(p, Q, U, nlos, layout, F_out);
+    if (st != RMS_OK) return st;
+    if (!out) return RMS_ERR_INVALID_ARG;
+    if (!is_tensor(p->precision) && (out->q_peak || out->u_peak || out->chi0)) return RMS_ERR_UNSUPPORTED;
+    if (*p->h_err) return RMS_ERR_TIMEOUT;
+    if (nlos == 0 ||
+        (!F_out && !out->peak_idx && !out->peak_abs && !out->phi_peak && !out->q_peak && !out->u_peak && !out->chi0))
+        return RMS_OK;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return RMS_ERR_CUDA;
+    PeakExtras x;
+    x.q = out->q_peak;
+    x.u = out->u_peak;
+    x.chi = out->chi0;
+    return synth_device(p, Q, U, nlos, layout, F_out, out->peak_idx, out->peak_abs, out->phi_peak,
+                        reinterpret_cast<cudaStream_t>(stream), x);
 }
 
 rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout, float *F_out,

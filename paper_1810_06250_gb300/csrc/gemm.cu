@@ -216,7 +216,10 @@ struct GemmParams {
     float *F;
     int32_t *pidx;
     float *pabs, *pphi;
+    float *pq, *pu, *pchi;      // optional: Re, Im of F at the peak and the angle chi0 there
     const float *phi32;
+    const double *phi64;
+    double lambda0sq;
     float out_scale;
     int32_t mode;
     const int8_t *rexp;
@@ -241,7 +244,7 @@ __host__ __device__ __forceinline__ uint32_t gemm_stage_bytes(int tile_n, int mo
 struct GSmem {
     uint8_t *ring;
     uint32_t stage_bytes;
-    float *epi, *pk_m;
+    float *epi, *pk_m, *pk_re, *pk_im;
     int *pk_i;
     uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;
     uint32_t *tmem_slot;
@@ -257,7 +260,9 @@ __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
     s.epi = reinterpret_cast<float *>(s.ring + (size_t)P.stages * s.stage_bytes);
     s.pk_m = s.epi + kEpiStageBytes / 4;
     s.pk_i = reinterpret_cast<int *>(s.pk_m + 2 * 4 * 32);
-    uint64_t *b = reinterpret_cast<uint64_t *>(s.pk_i + 2 * 4 * 32);
+    s.pk_re = reinterpret_cast<float *>(s.pk_i + 2 * 4 * 32);
+    s.pk_im = s.pk_re + 2 * 4 * 32;
+    uint64_t *b = reinterpret_cast<uint64_t *>(s.pk_im + 2 * 4 * 32);
     s.full = b;
     s.empty = s.full + P.stages;
     s.conv = s.empty + P.stages;
@@ -505,7 +510,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             const int64_t row = mt * kTileM + 32 * q + lane;
             float scale = P.out_scale;
             if (P.rexp != nullptr && row < nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
-            float bm = -1.0f;
+            float bm = -1.0f, br = 0.f, bim = 0.f;
             int bi = INT_MAX;
             for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
                 for (int g = 0; g < ngroups; ++g, ++g_all) {
@@ -549,7 +554,14 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                     const int k = kbase + p;
                     if (2 * p < ncols && k < P.nphi) {
                         const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
-                        if (m2 > bm) { bm = m2; bi = k; }
+                        if (m2 > bm) {
+                            bm = m2;
+                            bi = k;
+                            if constexpr (!ROT) {   // F at the peak (the window kernel has no use for it)
+                                br = fr;
+                                bim = fi;
+                            }
+                        }
                     }
                 }
                 if (P.F != nullptr) {
@@ -589,21 +601,36 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 if (!warp_wait(ebar, use_par ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
                 S.pk_m[(par * 4 + q) * 32 + lane] = bm;
                 S.pk_i[(par * 4 + q) * 32 + lane] = bi;
+                S.pk_re[(par * 4 + q) * 32 + lane] = br;
+                S.pk_im[(par * 4 + q) * 32 + lane] = bim;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(pbar);
             } else {
                 if (!warp_wait(pbar, use_par, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
                 const float om = S.pk_m[(par * 4 + q) * 32 + lane];
                 const int oi = S.pk_i[(par * 4 + q) * 32 + lane];
+                const float ore = S.pk_re[(par * 4 + q) * 32 + lane], oim = S.pk_im[(par * 4 + q) * 32 + lane];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(ebar);
-                if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; }
+                if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; br = ore; bim = oim; }
                 if (row < nlos) {
                     const int64_t orow = P.rows ? P.rows[row] : row;
                     const bool found = bi != INT_MAX;
                     if (P.pidx) P.pidx[orow] = found ? bi : -1;
                     if (P.pabs) P.pabs[orow] = found ? sqrtf(bm) : __int_as_float(0x7fc00000);
                     if (P.pphi) P.pphi[orow] = found ? P.phi32[bi] : __int_as_float(0x7fc00000);
+                    if (P.pq) P.pq[orow] = found ? br : __int_as_float(0x7fc00000);
+                    if (P.pu) P.pu[orow] = found ? bim : __int_as_float(0x7fc00000);
+                    if (P.pchi) {
+                        // chi0 = arg F(phi_peak) / 2 - phi_peak lambda_0^2, reduced to [0, pi)
+                        float c = __int_as_float(0x7fc00000);
+                        if (found) {
+                            double x = 0.5 * atan2((double)bim, (double)br) - P.phi64[bi] * P.lambda0sq;
+                            x -= M_PI * floor(x / M_PI);
+                            c = (float)x;
+                        }
+                        P.pchi[orow] = c;
+                    }
                 }
             }
         }
@@ -618,7 +645,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
     }
 }
 
-size_t gemm_fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 8 + 8 * 32 + 32; }
+size_t gemm_fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 16 + 8 * 32 + 32; }
 
 int gemm_stages(int tile_n, int mode)
 {
@@ -705,7 +732,12 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.pidx = o.pidx;
     P.pabs = o.pabs;
     P.pphi = o.pphi;
+    P.pq = o.pq;
+    P.pu = o.pu;
+    P.pchi = o.pchi;
     P.phi32 = p.d_phi32;
+    P.phi64 = p.d_phi;
+    P.lambda0sq = p.lambda0sq;
     P.out_scale = (float)(p.K * p.wmax);
     P.mode = mode;
     P.rexp = mode == MODE_FP16X3 ? o.rexp : nullptr;
@@ -764,7 +796,7 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
 
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
-                              cudaStream_t s, cudaEvent_t ev_mid)
+                              cudaStream_t s, cudaEvent_t ev_mid, float *pq, float *pu, float *pchi)
 {
     SplitOpts so;
     so.Q = Q;
@@ -785,6 +817,9 @@ cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *
     go.pidx = pidx;
     go.pabs = pabs;
     go.pphi = pphi;
+    go.pq = pq;
+    go.pu = pu;
+    go.pchi = pchi;
     go.rexp = rexp;
     return launch_gemm(p, go, s);
 }

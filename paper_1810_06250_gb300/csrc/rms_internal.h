@@ -127,6 +127,7 @@ struct GemmOpts {
     float *F = nullptr;
     int32_t *pidx = nullptr;
     float *pabs = nullptr, *pphi = nullptr;
+    float *pq = nullptr, *pu = nullptr, *pchi = nullptr;   // F at the peak, chi0
     const int8_t *rexp = nullptr;
     // window plans: rotate row r by T[clamp(centre[r], cmin, cmax)][.] ([.][ldT] float2)
     const int32_t *centre = nullptr;
@@ -139,7 +140,8 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
                                 const int64_t *count, int64_t nmax, uint8_t *dst, cudaStream_t s);
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
-                              cudaStream_t s, cudaEvent_t ev_mid = nullptr);
+                              cudaStream_t s, cudaEvent_t ev_mid = nullptr, float *pq = nullptr,
+                              float *pu = nullptr, float *pchi = nullptr);
 
 // generate.cu
 cudaError_t launch_generate(const rms_plan_s &p, const rms_source_model &m, int64_t los0, int64_t nlos,

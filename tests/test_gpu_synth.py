@@ -332,3 +332,54 @@ def test_synth_host_matches_device(rms, inputs, layout):
         i2 = torch.full((n,), -7, dtype=torch.int32).pin_memory()
         plan.synth_host(qh, uh, n, layout, None, i2)           # peak map only
         assert torch.equal(i2, i0.cpu())
+
+
+# ------------------------------------------------------------------- Q, U and chi0 at the peak
+@pytest.mark.parametrize("path", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("layout", ["chan", "los"])
+def test_peak_outputs(rms, inputs, oracle_mod, path, layout):
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = axes(inputs, cfg)
+    n = 3000
+    Q, U = inputs.make_cube(cfg, 4242, n)
+    dev = torch.device("cuda")
+    q = torch.from_numpy(inputs.to_layout(Q, layout)).to(dev)
+    u = torch.from_numpy(inputs.to_layout(U, layout)).to(dev)
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        F = torch.empty(n, cfg.nphi, 2, device=dev)
+        out = [torch.full((n,), -7, dtype=torch.int32, device=dev)] + [torch.full((n,), -7.0, device=dev) for _ in range(5)]
+        rms.rms_synth_peaks(plan.handle, q, u, n, layout, F, *out)
+        i0 = torch.empty(n, dtype=torch.int32, device=dev)
+        a0, p0 = torch.empty(n, device=dev), torch.empty(n, device=dev)
+        plan.synth(q, u, n, layout, None, i0, a0, p0)
+        plan.sync()
+        idx, ab, ph, qp, up, chi = [t.cpu().numpy() for t in out]
+        np.testing.assert_array_equal(idx, i0.cpu().numpy())      # same kernel, same peak map
+        np.testing.assert_array_equal(ab, a0.cpu().numpy())
+        np.testing.assert_array_equal(ph, p0.cpu().numpy())
+        Fg = F.cpu().numpy()
+        r = np.arange(n)
+        np.testing.assert_array_equal(qp, Fg[r, idx, 0])          # F itself at the peak
+        np.testing.assert_array_equal(up, Fg[r, idx, 1])
+        l0 = plan.rmsf()[0]
+        op = oracle_mod.plan(freq, "freq", w)
+        Fo = oracle_mod.synth(Q, U, op, phi)
+        fo = Fo[r, idx]
+        tol = gh.TOL[path] * np.abs(Fo).max(axis=1)
+        assert np.all(np.abs(qp - fo.real) <= tol) and np.all(np.abs(up - fo.imag) <= tol)
+        co = oracle_mod.chi0(fo, phi[idx], l0)
+        d = np.abs(chi.astype(np.float64) - co) % np.pi
+        d = np.minimum(d, np.pi - d)
+        # the angle's error is about |dF| / (2 |F|) plus FP32 rounding of the stored angle
+        assert np.all(d <= tol / np.abs(fo) + 1e-6), float((d / (tol / np.abs(fo) + 1e-6)).max())
+        assert np.all((chi >= 0) & (chi < np.pi + 1e-6))
+
+
+def test_peak_outputs_need_tensor_path(rms, inputs):
+    cfg = inputs.CONFIGS["tiny"]
+    freq, w, phi = axes(inputs, cfg)
+    z = torch.zeros(cfg.nchan * 4, device="cuda")
+    with rms.Plan(freq, phi, "fp32_table", weights=w) as plan:
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_synth_peaks(plan.handle, z, z, 4, "chan", None, None, None, None, z[:4])
+        assert e.value.status == rms.RMS_ERR_UNSUPPORTED
