@@ -8,7 +8,12 @@ phase matrix and RMSF are per-dataset constants, Sec. 2.3).  The metric is
 G(LOS * active channel * phi)/s.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--path bf16x3] [--layout chan]
+  python bench.py --config lofar_lr | lofar_hr [--peak-only]   (the paper's LOFAR cube shapes)
+  python bench.py --config learned   (the learned peak proposal against the full grid)
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+The cube is generated on the device by the seeded generator's device twin; the
+rows the CPU oracle checks are regenerated on the host.
 
 Multi-GPU (torchrun): every rank synthesises its own full cube (weak scaling,
 no collective on the data path); value = all ranks' units / max rank time.
@@ -47,6 +52,7 @@ def parse():
     ap.add_argument("--no-paths", action="store_true", help="skip timing the other precision paths")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--nlos", type=int, default=None, help="override the workload's LOS count (profiling runs)")
+    ap.add_argument("--peak-only", action="store_true", help="write the peak map only, no F cube")
     ap.add_argument("--n-train", type=int, default=1 << 20, help="learned workload: training LOS")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
     ap.add_argument("--hidden", type=int, default=256, help="learned workload: hidden units")
@@ -117,68 +123,35 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(cfg_name, nlos=None):
-    import dataclasses
-    from paper_1810_06250_gb300 import inputs
-    cfg = inputs.CONFIGS[cfg_name]
-    if nlos is not None:
-        cfg = dataclasses.replace(cfg, nlos=nlos)
-    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
-    Q, U = inputs.make_cube(cfg)
-    return inputs, cfg, freq, w, phi, Q, U
-
-
-def cpu_leg(cfg, freq, w, phi, Q, U, seconds, F_gpu_rows=None, rows=None):
-    """Time the FP64 oracle (as it stands) on a bounded LOS sample on all host cores.
-    Also returns the GPU-vs-FP64 error on the sampled rows when the GPU rows are given."""
-    import oracle
-    oracle.build()
-    op = oracle.plan(freq, "freq", w)
-    nact = int(np.count_nonzero(w))
-    # calibrate on 256 LOS, then size the sample for ~`seconds` of CPU work
-    t0 = time.perf_counter()
-    oracle.synth(Q[:256], U[:256], op, phi)
-    dt = time.perf_counter() - t0
-    n = int(min(cfg.nlos, max(256, 256 * seconds / max(dt, 1e-6))))
-    sel = rows if rows is not None else np.arange(n)
-    if rows is not None:
-        n = len(rows)
-    t0 = time.perf_counter()
-    Fo = oracle.synth(Q[sel], U[sel], op, phi)
-    dt = time.perf_counter() - t0
-    units = n * nact * len(phi)
-    out = {"value": units / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-           "sample": "%d of %d LOS (all %d active channels x %d phi), FP64 C oracle, OpenMP over LOS, %.1f s"
-                     % (n, cfg.nlos, nact, len(phi), dt)}
-    err = None
-    if F_gpu_rows is not None:
-        d = np.abs(F_gpu_rows - Fo)
-        per = d.max(axis=1) / np.abs(Fo).max(axis=1)
-        err = {"per_los_max": float(per.max()), "per_los_p999": float(np.quantile(per, 0.999)),
-               "cube": float(d.max() / np.abs(Fo).max()), "sample_los": int(n)}
-    return out, err
-
-
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    _, cfg, freq, w, phi, Q, U = make_inputs(args.config, args.nlos)
+    import dataclasses
+    from paper_1810_06250_gb300 import inputs
+    cfg = inputs.CONFIGS[args.config]
+    if args.nlos is not None:
+        cfg = dataclasses.replace(cfg, nlos=args.nlos)
+    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
     import oracle
     oracle.build()
     op = oracle.plan(freq, "freq", w)
     nact = int(np.count_nonzero(w))
-    # each step = a bounded sample so that the whole run ends within a few minutes
+    # each step = a bounded sample so that the whole run ends within a few minutes; the
+    # sample's LOS are generated on the host as they are needed
     budget = 150.0
+    Q, U = inputs.make_cube(cfg, 0, 32)
     t0 = time.perf_counter()
-    oracle.synth(Q[:128], U[:128], op, phi)
-    per_los = (time.perf_counter() - t0) / 128
+    oracle.synth(Q, U, op, phi)
+    per_los = (time.perf_counter() - t0) / 32
     n = int(max(16, min(cfg.nlos, budget / max(1, args.steps + args.warmup) / per_los)))
+    pool = min(cfg.nlos, 4 * n)
+    Q, U = inputs.make_cube(cfg, 0, pool)
     for i in range(args.warmup):
         oracle.synth(Q[:n], U[:n], op, phi)
     times = []
     for i in range(args.steps):
-        s = (i * n) % max(1, cfg.nlos - n)
+        s = (i * n) % max(1, pool - n)
         t0 = time.perf_counter()
         oracle.synth(Q[s:s + n], U[s:s + n], op, phi)
         times.append(time.perf_counter() - t0)
@@ -212,10 +185,12 @@ def measured_traffic(kernel_src: str, summary: str):
     return None
 
 
-def workload_name(cfg, nact, layout):
-    return ("%s: %dx%d LOS x %d channels (%d active) %.0f-%.0f MHz x %d phi in [%g, %g] rad/m^2, FP32 Q/U %s-major, "
-            "complex64 F + peak map" % (cfg.name, int(round(cfg.nlos ** 0.5)), int(round(cfg.nlos ** 0.5)), cfg.nchan,
-                                        nact, cfg.nu0 / 1e6, cfg.nu1 / 1e6, cfg.nphi, cfg.phi_min, cfg.phi_max, layout))
+def workload_name(cfg, nact, layout, peak_only=False):
+    side = int(round(cfg.nlos ** 0.5))
+    shape = "%dx%d LOS" % (side, side) if side * side == cfg.nlos else "%d LOS" % cfg.nlos
+    return ("%s: %s x %d channels (%d active) %.3f-%.3f MHz x %d phi in [%g, %g] rad/m^2, FP32 Q/U %s-major, %s"
+            % (cfg.name, shape, cfg.nchan, nact, cfg.nu0 / 1e6, cfg.nu1 / 1e6, cfg.nphi, cfg.phi_min, cfg.phi_max,
+               layout, "peak map only" if peak_only else "complex64 F + peak map"))
 
 
 def time_steps(fn, stream, steps, warmup, torch, barrier=None):
@@ -238,9 +213,23 @@ def time_steps(fn, stream, steps, warmup, torch, barrier=None):
     return total, per
 
 
+def sample_rows(cfg, n, rng):
+    """About n LOS in 64-row blocks spread over the cube: (rows, host Q, host U) regenerated on the
+    host by the seeded generator (inputs.make_cube), as the oracle's input."""
+    from paper_1810_06250_gb300 import inputs
+    blk = 64
+    nb = max(1, min(n // blk, cfg.nlos // blk))
+    starts = np.sort(rng.choice(cfg.nlos // blk, nb, replace=False)) * blk
+    Qs, Us = zip(*(inputs.make_cube(cfg, int(s0), blk) for s0 in starts))
+    rows = (starts[:, None] + np.arange(blk)[None, :]).ravel()
+    return rows, np.concatenate(Qs), np.concatenate(Us)
+
+
 def run_ours(args):
+    import dataclasses
     import torch
     import paper_1810_06250_gb300 as rms
+    from paper_1810_06250_gb300 import inputs, learned as Lm
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -248,16 +237,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rms.build()
-    inputs, cfg, freq, w, phi, Q, U = make_inputs(args.config, args.nlos)
+    cfg = inputs.CONFIGS[args.config]
+    if args.nlos is not None:
+        cfg = dataclasses.replace(cfg, nlos=args.nlos)
+    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
     nact = int(np.count_nonzero(w))
     L = cfg.nlos
-    from paper_1810_06250_gb300.inputs import to_layout
-    q = torch.from_numpy(to_layout(Q, args.layout)).to(dev)
-    u = torch.from_numpy(to_layout(U, args.layout)).to(dev)
-    F = torch.empty(L, cfg.nphi, 2, device=dev)
-    pidx = torch.empty(L, dtype=torch.int32, device=dev)
-    pabs = torch.empty(L, device=dev)
-    pphi = torch.empty(L, device=dev)
+    peak_only = args.peak_only or L * cfg.nphi * 8 > 64e9     # F of the 4000^2 x 7000 cube is 0.9 TB
     stream = torch.cuda.Stream(dev)
     units = L * nact * cfg.nphi
     barrier = None
@@ -268,6 +254,12 @@ def run_ours(args):
     t_plan0 = time.perf_counter()
     plan = rms.Plan(freq, phi, args.path, weights=w, device=local)
     plan_ms = 1e3 * (time.perf_counter() - t_plan0)
+    # the cube is generated on the device by the seeded generator's device twin
+    q, u = Lm.generate(plan.handle, cfg, 0, L, args.layout)
+    F = None if peak_only else torch.empty(L, cfg.nphi, 2, device=dev)
+    pidx = torch.empty(L, dtype=torch.int32, device=dev)
+    pabs = torch.empty(L, device=dev)
+    pphi = torch.empty(L, device=dev)
 
     def step():
         plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
@@ -289,7 +281,7 @@ def run_ours(args):
     value, tmax = throughput(units, args.steps, total_ms, world, dev)
     avg_launch_ms = statistics.mean(per)
 
-    # roofline of the dominant kernel (the synthesis kernel: one launch per step)
+    # roofline of the dominant kernel (the contraction: one launch per step)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -297,7 +289,7 @@ def run_ours(args):
         pass
     useful_flops = 8.0 * units
     terms = 1 if args.path == "bf16" else 3
-    hbm_bytes = L * (8.0 * (nact if args.layout == "chan" else cfg.nchan) + 8.0 * cfg.nphi + 12.0)
+    hbm_bytes = L * (8.0 * (nact if args.layout == "chan" else cfg.nchan) + (0 if peak_only else 8.0 * cfg.nphi) + 12.0)
     if tensor_path:
         peak = peaks.get("bf16_tflops_sustained")
         src = "measured sustained bf16 (MEASURED_PEAKS.json)" if peak else "fallback 1700 TFLOP/s sustained"
@@ -306,8 +298,8 @@ def run_ours(args):
         gemm_launch_ms = gemm_ms / max(1, ncalls)
         achieved = useful_flops / (gemm_launch_ms * 1e-3) / 1e12
         traffic = measured_traffic("gemm.cu", "gemm_lofar_bf16x3.md") \
-            if (args.path == "bf16x3" and args.layout == "chan" and args.config == CONFIG_NAME and args.nlos is None) \
-            else None
+            if (args.path == "bf16x3" and args.layout == "chan" and args.config == CONFIG_NAME and args.nlos is None
+                and not peak_only) else None
         roof = {"kernel": "gemm_kernel (tensor-core contraction)", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)", "peak_source": src,
@@ -325,20 +317,26 @@ def run_ours(args):
         peak = props.multi_processor_count * 128 * 2 * clk_mhz * 1e6 / 1e12
         achieved = useful_flops / (avg_launch_ms * 1e-3) / 1e12
         traffic = measured_traffic("simt.cu", "simt_lofar_fp32_table.md") \
-            if (args.path == "fp32_table" and args.layout == "chan" and args.config == CONFIG_NAME) else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            if (args.path == "fp32_table" and args.layout == "chan" and args.config == CONFIG_NAME
+                and args.nlos is None and not peak_only) else None
+        roof = {"kernel": "simt_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock",
                 "hbm_gbs": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9}
 
+    in_gb = L * cfg.nchan * 8 / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.path, "data": "synthetic",
-            "config": {"workload": workload_name(cfg, nact, args.layout), "nlos_per_gpu": L, "nchan": cfg.nchan,
-                       "nchan_active": nact, "nphi": cfg.nphi, "layout": args.layout,
-                       "l2": "inputs larger than L2 (0.84 GB in, 0.84 GB out per step)",
+            "config": {"workload": workload_name(cfg, nact, args.layout, peak_only), "nlos_per_gpu": L,
+                       "nchan": cfg.nchan, "nchan_active": nact, "nphi": cfg.nphi, "layout": args.layout,
+                       "l2": "inputs larger than L2 (%.2f GB in%s per step)"
+                             % (in_gb, "" if peak_only else ", %.2f GB out" % (L * cfg.nphi * 8 / 1e9)),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "units_per_step_total_channels": L * cfg.nchan * cfg.nphi},
+                       "units_per_step_total_channels": L * cfg.nchan * cfg.nphi,
+                       "inputs": "device-generated by the seeded generator's device twin; the CPU sample is "
+                                 "regenerated on the host"},
             "roofline": roof, "gpu_launches": args.steps * (2 if tensor_path else 1),
             "plan_ms": plan_ms, "clocks": clk.summary()}
 
@@ -362,10 +360,10 @@ def run_ours(args):
         plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
         plan.sync(stream)
 
-    if rank == 0 and world == 1 and not args.no_e2e:
-        Qh = torch.from_numpy(to_layout(Q, args.layout)).pin_memory()
-        Uh = torch.from_numpy(to_layout(U, args.layout)).pin_memory()
-        Fh = torch.empty(L, cfg.nphi, 2).pin_memory()
+    if rank == 0 and world == 1 and not args.no_e2e and in_gb < 32:
+        Qh = q.cpu().pin_memory()
+        Uh = u.cpu().pin_memory()
+        Fh = None if peak_only else torch.empty(L, cfg.nphi, 2).pin_memory()
         ih = torch.empty(L, dtype=torch.int32).pin_memory()
         ah = torch.empty(L).pin_memory()
         ph = torch.empty(L).pin_memory()
@@ -380,25 +378,42 @@ def run_ours(args):
         dt = (time.perf_counter() - t0) / n_e2e
         line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
                        "h2d_bytes_per_step": int(Qh.numel() * 4 + Uh.numel() * 4),
-                       "d2h_bytes_per_step": int(Fh.numel() * 4 + L * 12),
-                       "how": "rms_synth_host: pinned host Q/U -> device, synthesis, F and peak map -> pinned host, sync"}
+                       "d2h_bytes_per_step": int((0 if Fh is None else Fh.numel() * 4) + L * 12),
+                       "how": "rms_synth_host: pinned host Q/U -> device in LOS chunks, synthesis, F and peak "
+                              "map -> pinned host, copies overlapped on three streams, sync"}
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        rng = np.random.default_rng(12345)
-        sel = None
-        # size the sample from a calibration run, then check the GPU rows on it
         import oracle
         oracle.build()
         op = oracle.plan(freq, "freq", w)
+        Qc, Uc = inputs.make_cube(cfg, 0, 32)
         t0 = time.perf_counter()
-        oracle.synth(Q[:128], U[:128], op, phi)
-        per_los = (time.perf_counter() - t0) / 128
+        oracle.synth(Qc, Uc, op, phi)
+        per_los = (time.perf_counter() - t0) / 32
         n = int(min(L, max(256, args.cpu_seconds / per_los)))
-        sel = np.sort(rng.choice(L, n, replace=False))
-        Fg = F[torch.from_numpy(sel).to(dev)].cpu().numpy()
-        cpu, err = cpu_leg(cfg, freq, w, phi, Q, U, args.cpu_seconds, Fg[..., 0] + 1j * Fg[..., 1], sel)
-        line["cpu_baseline"] = cpu
-        line["error_vs_fp64"] = err
+        rows, Qs, Us = sample_rows(cfg, n, np.random.default_rng(12345))
+        t0 = time.perf_counter()
+        Fo = oracle.synth(Qs, Us, op, phi)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(rows) * nact * cfg.nphi / dt / 1e9, "unit": UNIT,
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "%d of %d LOS in 64-LOS blocks (all %d active channels x %d phi), FP64 C "
+                                          "oracle, OpenMP over LOS, %.1f s" % (len(rows), L, nact, cfg.nphi, dt)}
+        sel = torch.from_numpy(rows).to(dev)
+        if F is not None:
+            Fg = F[sel].cpu().numpy()
+            Fg = Fg[..., 0] + 1j * Fg[..., 1]
+            d = np.abs(Fg - Fo)
+            per_los = d.max(axis=1) / np.abs(Fo).max(axis=1)
+            line["error_vs_fp64"] = {"per_los_max": float(per_los.max()),
+                                     "per_los_p999": float(np.quantile(per_los, 0.999)),
+                                     "cube": float(d.max() / np.abs(Fo).max()), "sample_los": int(len(rows))}
+        else:
+            oi, oa = oracle.peak(Fo)
+            ga = pabs[sel].cpu().numpy()
+            line["error_vs_fp64"] = {"peak_abs_rel_max": float(np.max(np.abs(ga - oa) / np.abs(Fo).max(axis=1))),
+                                     "peak_idx_equal": float(np.mean(pidx[sel].cpu().numpy() == oi)),
+                                     "sample_los": int(len(rows))}
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

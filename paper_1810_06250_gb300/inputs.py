@@ -101,6 +101,12 @@ CONFIGS = {
     # MWA-like large phases: 1024^2 LOS, 1536 channels 72-231 MHz, 4001 phi in +-2000
     "mwa": CubeConfig("mwa", 1024 * 1024, 1536, 72e6, 231e6, 4001, -2000.0, 2000.0, seed=1004,
                       phi0=(-1800.0, 1800.0)),
+    # the paper's LOFAR benchmark shapes (Sec. 3.3): 856 channels 120.238-166.087 MHz,
+    # 7000 phi to about +-350 rad/m^2; low resolution 540^2 LOS, high resolution 4000^2
+    "lofar_lr": CubeConfig("lofar_lr", 540 * 540, 856, 120.238e6, 166.087e6, 7000, -350.0, 350.0, seed=1006,
+                           phi0=(-300.0, 300.0), slab_prob=0.5, slab_w=10.0, sigma=0.005),
+    "lofar_hr": CubeConfig("lofar_hr", 4000 * 4000, 856, 120.238e6, 166.087e6, 7000, -350.0, 350.0, seed=1007,
+                           phi0=(-300.0, 300.0), slab_prob=0.5, slab_w=10.0, sigma=0.005),
     # learned-proposal workload: 2048^2 LOS on the LOFAR band and grid, SNR 5-100,
     # thin components and Burn slabs mixed as on the LOFAR cube
     "learned": CubeConfig("learned", 2048 * 2048, 400, 115e6, 178e6, 401, -100.0, 100.0, seed=1005,

@@ -240,23 +240,24 @@ def test_lofar_full(rms, inputs, oracle_mod, lofar, path, layout):
 
 # ------------------------------------------------------------------- large cubes
 LARGE = [("precision", "bf16x3", 2048), ("precision", "bf16", 512), ("precision", "fp32_fly", 512),
-         ("precision", "fp32_table", 512), ("mwa", "bf16x3", 256), ("mwa", "fp16x3", 256)]
+         ("precision", "fp32_table", 512), ("mwa", "bf16x3", 256), ("mwa", "fp16x3", 256),
+         ("lofar_lr", "bf16x3", 256)]
 
 
 @pytest.mark.parametrize("cfg_name,path,nsample", LARGE)
 def test_large_full(rms, inputs, oracle_mod, cfg_name, path, nsample):
-    """Full-size 2048^2 x 800 x 1001 and 1024^2 x 1536 x 4001 cubes in the launch
-    configuration the benchmark uses.  The device cube repeats a host-generated
-    base block of 16384 LOS (row l holds base row l % 16384); sampled rows are
-    compared with the oracle on the base rows and their peaks checked."""
+    """Full-size 2048^2 x 800 x 1001, 1024^2 x 1536 x 4001 and 540^2 x 856 x 7000 cubes
+    in the launch configuration the benchmark uses.  The device cube repeats a
+    host-generated base block of 16384 LOS (row l holds base row l % 16384); sampled
+    rows are compared with the oracle on the base rows and their peaks checked."""
     cfg = inputs.CONFIGS[cfg_name]
     freq, w, phi = axes(inputs, cfg)
     nbase = 16384
     Qb, Ub = inputs.make_cube(cfg, 0, nbase)
-    reps = cfg.nlos // nbase
+    reps = (cfg.nlos + nbase - 1) // nbase
     dev = torch.device("cuda")
-    q = torch.from_numpy(np.ascontiguousarray(Qb.T)).to(dev).repeat(1, reps)      # chan-major [nchan][nlos]
-    u = torch.from_numpy(np.ascontiguousarray(Ub.T)).to(dev).repeat(1, reps)
+    q = torch.from_numpy(np.ascontiguousarray(Qb.T)).to(dev).repeat(1, reps)[:, :cfg.nlos].contiguous()
+    u = torch.from_numpy(np.ascontiguousarray(Ub.T)).to(dev).repeat(1, reps)[:, :cfg.nlos].contiguous()
     rng = np.random.default_rng(4242)
     sample = np.unique(np.r_[0, cfg.nlos - 1, rng.choice(cfg.nlos, nsample - 2, replace=False)])
     op = oracle_mod.plan(freq, "freq", w)
