@@ -258,6 +258,17 @@ rms_status rms_plan_set_timeout(rms_plan_t plan, int64_t ns);
 rms_status rms_plan_set_kernel_timing(rms_plan_t plan, int32_t enable);
 rms_status rms_plan_kernel_times(rms_plan_t plan, double *split_ms, double *contract_ms, int64_t *calls);
 
+/*
+ * Self-test of the device failure path (the paper has no counterpart): launches
+ * a kernel that waits, with the same bounded wait as every pipeline wait of the
+ * tensor-core kernels, on a barrier nothing ever arrives on.  The wait gives up
+ * after limit_ns (1 .. 1e10), records RMS_ERR_TIMEOUT on the plan (reported and
+ * cleared by the next rms_plan_sync) and the kernel returns; the context stays
+ * usable.  outcome (host): 2 when the wait gave up as it must, 1 if it
+ * completed.  Synchronous.
+ */
+rms_status rms_selftest_wait_timeout(rms_plan_t plan, int64_t limit_ns, int32_t *outcome);
+
 /* ==========================================================================
  * Synthetic sources on the device (Sec. 2.1 source models)
  * ========================================================================== */

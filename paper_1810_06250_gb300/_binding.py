@@ -35,7 +35,7 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_plan_set_timeout", "rms_generate", "rms_net_create", "rms_net_destroy", "rms_net_info",
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
-           "rms_plan_kernel_times", "rms_synth_peaks")
+           "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
             "rms_generate": [P, P, _i64, _i64, _i32, P, P, P],
             "rms_plan_set_kernel_timing": [P, _i32],
             "rms_synth_peaks": [P, P, P, _i64, _i32, P, P, P],
+            "rms_selftest_wait_timeout": [P, _i64, P],
             "rms_plan_kernel_times": [P, P, P, P],
             "rms_net_create": [ctypes.POINTER(P), P, _i32, _i32, ctypes.c_uint64],
             "rms_net_destroy": [P],
@@ -380,3 +381,10 @@ def rms_synth_peaks(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=Non
     st = load().rms_synth_peaks(plan, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
                                 _layout(layout), _dptr(F_out, None, "F_out"), ctypes.byref(out), _stream(stream))
     _check(st, "rms_synth_peaks")
+
+
+def rms_selftest_wait_timeout(plan: int, limit_ns: int) -> int:
+    """Run the bounded-wait self-test; returns 2 when the wait gave up (see include/rms.h)."""
+    out = _i32()
+    _check(load().rms_selftest_wait_timeout(plan, int(limit_ns), ctypes.byref(out)), "rms_selftest_wait_timeout")
+    return out.value

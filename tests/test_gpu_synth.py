@@ -384,3 +384,23 @@ def test_peak_outputs_need_tensor_path(rms, inputs):
         with pytest.raises(rms.RmsError) as e:
             rms.rms_synth_peaks(plan.handle, z, z, 4, "chan", None, None, None, None, z[:4])
         assert e.value.status == rms.RMS_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------- failure detection
+def test_bounded_wait_gives_up_and_reports(rms, inputs):
+    """A wait that cannot complete gives up after its limit, the plan reports
+    RMS_ERR_TIMEOUT once, and the context and plan keep working."""
+    cfg = inputs.CONFIGS["tiny"]
+    freq, w, phi = axes(inputs, cfg)
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        import time
+        t0 = time.perf_counter()
+        assert rms.rms_selftest_wait_timeout(plan.handle, 20_000_000) == 2       # 20 ms limit
+        assert time.perf_counter() - t0 < 5.0
+        with pytest.raises(rms.RmsError) as e:
+            plan.sync()
+        assert e.value.status == rms.RMS_ERR_TIMEOUT
+        plan.sync()                                                               # cleared
+        Q, U = inputs.make_cube(cfg)
+        F, pidx, pabs, pphi = run(rms, plan, Q, U, "chan", cfg.nlos)              # still synthesises
+        assert np.all(pidx >= 0)
