@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--nlos", type=int, default=None, help="override the workload's LOS count (profiling runs)")
     ap.add_argument("--peak-only", action="store_true", help="write the peak map only, no F cube")
+    ap.add_argument("--no-clean", action="store_true", help="skip timing RM-CLEAN of the synthesised cube")
     ap.add_argument("--n-train", type=int, default=1 << 20, help="learned workload: training LOS")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
     ap.add_argument("--hidden", type=int, default=256, help="learned workload: hidden units")
@@ -340,6 +341,26 @@ def run_ours(args):
             "roofline": roof, "gpu_launches": args.steps * (2 if tensor_path else 1),
             "plan_ms": plan_ms, "clocks": clk.summary()}
 
+    if rank == 0 and world == 1 and not args.no_clean and F is not None and cfg.nphi <= 2048 and tensor_path:
+        # RM-CLEAN of the synthesised cube (FP64 Hogbom iterations, one warp per LOS)
+        sigma_f = cfg.sigma * float(np.sqrt(np.sum(w * w)) / np.sum(w))
+        thr = 5.0 * sigma_f
+        c = rms.rms_clean_create(plan.handle)
+        Fc = torch.empty_like(F)
+        nit = torch.empty(L, dtype=torch.int32, device=dev)
+
+        def clean_step():
+            rms.rms_clean(c, F, L, 0.1, 1000, thr, Fc, None, None, nit, stream)
+        with torch.cuda.stream(stream):
+            t_cl, _ = time_steps(clean_step, stream, 3, 1, torch)
+        rms.rms_clean_destroy(c)
+        mean_it = float(nit.double().mean().item())
+        line["clean"] = {"ms_per_call": t_cl / 3, "los_per_s": L / (t_cl / 3 * 1e-3), "gain": 0.1,
+                         "max_iter": 1000, "threshold": thr, "threshold_rule": "5 sigma_F",
+                         "mean_iterations": mean_it, "precision": "f64",
+                         "component_updates_per_s": L * mean_it * cfg.nphi / (t_cl / 3 * 1e-3)}
+        del Fc, nit
+
     if rank == 0 and world == 1 and not args.no_paths:
         paths = {}
         for p in ("fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3"):
@@ -400,6 +421,14 @@ def run_ours(args):
                                 "sample": "%d of %d LOS in 64-LOS blocks (all %d active channels x %d phi), FP64 C "
                                           "oracle, OpenMP over LOS, %.1f s" % (len(rows), L, nact, cfg.nphi, dt)}
         sel = torch.from_numpy(rows).to(dev)
+        if "clean" in line:
+            from oracle import clean as oclean
+            dphi = float(phi[1] - phi[0])
+            R2 = oracle.rmsf(op, (np.arange(2 * len(phi) - 1) - (len(phi) - 1)) * dphi)
+            k = min(len(rows), 256)
+            t0 = time.perf_counter()
+            oclean.clean(Fo[:k], R2, 0.1, 1000, line["clean"]["threshold"], oracle.fwhm_measured(op), dphi)
+            line["clean"]["cpu_oracle_los_per_s"] = k / (time.perf_counter() - t0)
         if F is not None:
             Fg = F[sel].cpu().numpy()
             Fg = Fg[..., 0] + 1j * Fg[..., 1]

@@ -270,6 +270,43 @@ rms_status rms_plan_kernel_times(rms_plan_t plan, double *split_ms, double *cont
 rms_status rms_selftest_wait_timeout(rms_plan_t plan, int64_t limit_ns, int32_t *outcome);
 
 /* ==========================================================================
+ * RM-CLEAN (named after synthesis in Sec. 2.2 and Sec. 4; the paper gives no
+ * algorithm: this is the Hogbom form used for RM synthesis)
+ *
+ * For each LOS, starting from res = F (a dirty spectrum from rms_synth), repeat
+ * at most max_iter times:
+ *     j = argmax_k |res_k| (lowest index on ties; NaN never chosen)
+ *     stop when |res_j| < threshold (or no |res| is finite)
+ *     c = gain res_j;  comp_j += c;  res_k -= c R(phi_k - phi_j) for every k
+ * then restore  clean_k = res_k + sum_{|d| <= W} comp_{k-d} exp(-4 ln2 (d dphi)^2 / fwhm^2),
+ * W = ceil(3 fwhm / dphi) (at most nphi - 1).  The plan's phi grid must be
+ * uniform (step dphi), with 2 <= nphi <= 2048.  The iteration runs in FP64, every
+ * product and sum rounded separately, so that with the same R table the device
+ * makes the same choices as the FP64 definition.
+ * ========================================================================== */
+typedef struct rms_clean_s *rms_clean_t;
+
+/*
+ * fwhm: the restoring beam's FWHM in rad m^-2 (<= 0: the plan's measured RMSF
+ * FWHM).  R2_host: NULL to build R at the 2 nphi - 1 offsets (m - nphi + 1)
+ * dphi on the device in FP64 (Eq. Rsum), or a host array of those values
+ * [2 nphi - 1][2] (re, im) to use instead.  RMS_ERR_INVALID_ARG for a
+ * non-uniform or too long grid.  Synchronous.  The plan must outlive the object.
+ */
+rms_status rms_clean_create(rms_clean_t *clean, rms_plan_t plan, double fwhm, const double *R2_host);
+rms_status rms_clean_destroy(rms_clean_t clean);
+
+/*
+ * F: device [nlos][nphi] complex64 dirty spectra (8-byte aligned).  gain in
+ * (0, 1]; threshold >= 0 in |F| units; max_iter >= 0.  Outputs (device, any may
+ * be NULL): F_clean, residual, components [nlos][nphi] complex64 (rounded from
+ * FP64); niter [nlos] int32, the iterations performed.  Asynchronous on stream.
+ */
+rms_status rms_clean(rms_clean_t clean, const float *F, int64_t nlos, float gain, int32_t max_iter,
+                     float threshold, float *F_clean, float *residual, float *components, int32_t *niter,
+                     void *stream);
+
+/* ==========================================================================
  * Synthetic sources on the device (Sec. 2.1 source models)
  * ========================================================================== */
 

@@ -35,7 +35,8 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_plan_set_timeout", "rms_generate", "rms_net_create", "rms_net_destroy", "rms_net_info",
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
-           "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout")
+           "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout", "rms_clean_create",
+           "rms_clean_destroy", "rms_clean")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
             "rms_plan_set_kernel_timing": [P, _i32],
             "rms_synth_peaks": [P, P, P, _i64, _i32, P, P, P],
             "rms_selftest_wait_timeout": [P, _i64, P],
+            "rms_clean_create": [ctypes.POINTER(P), P, ctypes.c_double, P],
+            "rms_clean_destroy": [P],
+            "rms_clean": [P, P, _i64, ctypes.c_float, _i32, ctypes.c_float, P, P, P, P, P],
             "rms_plan_kernel_times": [P, P, P, P],
             "rms_net_create": [ctypes.POINTER(P), P, _i32, _i32, ctypes.c_uint64],
             "rms_net_destroy": [P],
@@ -388,3 +392,28 @@ def rms_selftest_wait_timeout(plan: int, limit_ns: int) -> int:
     out = _i32()
     _check(load().rms_selftest_wait_timeout(plan, int(limit_ns), ctypes.byref(out)), "rms_selftest_wait_timeout")
     return out.value
+
+
+def rms_clean_create(plan: int, fwhm: float = 0.0, R2_host=None) -> int:
+    """RM-CLEAN object for a plan with a uniform phi grid (include/rms.h); R2_host: optional
+    complex128 numpy array of R at the 2 nphi - 1 offsets."""
+    out = _c_void_p()
+    r2 = None
+    if R2_host is not None:
+        r2 = np.ascontiguousarray(np.stack([np.real(R2_host), np.imag(R2_host)], axis=-1), dtype=np.float64)
+    _check(load().rms_clean_create(ctypes.byref(out), plan, float(fwhm), None if r2 is None else r2.ctypes.data),
+           "rms_clean_create")
+    return out.value
+
+
+def rms_clean_destroy(c: int):
+    _check(load().rms_clean_destroy(c), "rms_clean_destroy")
+
+
+def rms_clean(c: int, F, nlos: int, gain: float, max_iter: int, threshold: float, F_clean=None, residual=None,
+              components=None, niter=None, stream=None):
+    import torch
+    st = load().rms_clean(c, _dptr(F, None, "F"), int(nlos), float(gain), int(max_iter), float(threshold),
+                          _dptr(F_clean, None, "F_clean"), _dptr(residual, None, "residual"),
+                          _dptr(components, None, "components"), _dptr(niter, torch.int32, "niter"), _stream(stream))
+    _check(st, "rms_clean")
