@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-paths", action="store_true", help="skip timing the other precision paths")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nlos", type=int, default=None, help="override the workload's LOS count (profiling runs)")
     ap.add_argument("--peak-only", action="store_true", help="write the peak map only, no F cube")
     ap.add_argument("--no-clean", action="store_true", help="skip timing RM-CLEAN of the synthesised cube")
@@ -407,10 +407,12 @@ def run_ours(args):
         import oracle
         oracle.build()
         op = oracle.plan(freq, "freq", w)
-        Qc, Uc = inputs.make_cube(cfg, 0, 32)
+        # calibrate on enough LOS to keep every host core busy, then size the sample
+        ncal = int(min(L, 64 * max(1, oracle.num_threads())))
+        Qc, Uc = inputs.make_cube(cfg, 0, ncal)
         t0 = time.perf_counter()
         oracle.synth(Qc, Uc, op, phi)
-        per_los = (time.perf_counter() - t0) / 32
+        per_los = (time.perf_counter() - t0) / ncal
         n = int(min(L, max(256, args.cpu_seconds / per_los)))
         rows, Qs, Us = sample_rows(cfg, n, np.random.default_rng(12345))
         t0 = time.perf_counter()
