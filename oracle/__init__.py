@@ -225,3 +225,44 @@ def chi0(F_peak, phi_peak, lambda0sq):
     F_peak = np.asarray(F_peak)
     x = 0.5 * np.arctan2(F_peak.imag, F_peak.real) - np.asarray(phi_peak, dtype=np.float64) * lambda0sq
     return x - np.pi * np.floor(x / np.pi)
+
+
+def refine_peak(F, phi, idx):
+    """Sub-grid peak: the vertex of the parabola through |F| at phi[k-1], phi[k], phi[k+1], k = idx.
+
+    The paper reports the grid sample where |F| peaks (Sec. 2.2); this
+    interpolates between samples.  The parabola is the exact quadratic
+    interpolant of the three points (numpy.polyfit of degree 2, in t = phi -
+    phi[k]); its vertex t* = -c1 / (2 c2) is kept inside [phi[k-1], phi[k+1]].
+    Where the vertex is undefined -- k at an end of the grid, an interpolant
+    that is not concave (c2 >= 0), a non-finite neighbour, or both neighbours
+    on one side of phi[k] -- the sample itself is returned.  NaN where idx < 0.
+
+    F: complex [nlos][nphi]; phi: [nphi]; idx: int [nlos].
+    Returns (phi_ref, abs_ref), float64 [nlos].
+    """
+    F = np.atleast_2d(np.asarray(F))
+    phi = np.asarray(phi, dtype=np.float64)
+    idx = np.asarray(idx)
+    nlos, nphi = F.shape
+    phi_ref = np.full(nlos, np.nan)
+    abs_ref = np.full(nlos, np.nan)
+    for l in range(nlos):
+        k = int(idx[l])
+        if k < 0 or k >= nphi:
+            continue
+        y = np.abs(F[l].astype(np.complex128))
+        phi_ref[l], abs_ref[l] = phi[k], y[k]
+        if k == 0 or k == nphi - 1:
+            continue
+        t = phi[k - 1:k + 2] - phi[k]
+        yy = y[k - 1:k + 2]
+        if not (t[0] * t[2] < 0.0) or not np.all(np.isfinite(yy)):
+            continue
+        c2, c1, c0 = np.polyfit(t, yy, 2)
+        if not c2 < 0.0:
+            continue
+        ts = min(max(-c1 / (2.0 * c2), min(t[0], t[2])), max(t[0], t[2]))
+        phi_ref[l] = phi[k] + ts
+        abs_ref[l] = np.polyval([c2, c1, c0], ts)
+    return phi_ref, abs_ref
