@@ -164,6 +164,28 @@ rms_status rms_synth_peaks(rms_plan_t plan, const float *Q, const float *U, int6
                            float *F_out, const rms_peak_outputs *out, void *stream);
 
 /*
+ * Sub-grid peak refinement (the paper reports the grid sample where |F| peaks,
+ * Sec. 2.2; this interpolates between samples): for each LOS, the vertex of the
+ * parabola through |F| at phi_{k-1}, phi_k, phi_{k+1}, k = peak_idx[l].  With
+ * d0 = phi_{k-1} - phi_k, d2 = phi_{k+1} - phi_k and y = |F| (FP64 from the
+ * stored FP32 values):
+ *     a = ((y_{k-1} - y_k) / d0 - (y_{k+1} - y_k) / d2) / (d0 - d2)
+ *     b = (y_{k-1} - y_k) / d0 - a d0,   t* = -b / (2a) clamped to [d0, d2]
+ *     phi_ref = phi_k + t*,   abs_ref = y_k + b t* + a t*^2
+ * computed in FP64, rounded to FP32.  Where that is undefined -- k at either end
+ * of the grid, a >= 0, a NaN neighbour, or neighbours on the same side of phi_k
+ * (a non-monotonic grid) -- phi_ref = phi_k and abs_ref = |F_k|.  NaN for both
+ * where peak_idx is -1 (or out of range).
+ *   F        device [nlos][nphi] complex64 from rms_synth (8-byte aligned)
+ *   peak_idx device [nlos] int32 from the same call
+ *   phi_ref, abs_ref  device [nlos] float, either may be NULL
+ * Asynchronous on stream; allocates nothing.  RMS_ERR_INVALID_ARG for a NULL
+ * plan, F or peak_idx, nlos < 0, or a misaligned F.
+ */
+rms_status rms_refine_peaks(rms_plan_t plan, const float *F, int64_t nlos, const int32_t *peak_idx,
+                            float *phi_ref, float *abs_ref, void *stream);
+
+/*
  * rms_synth from HOST buffers: copies Q and U to the device, synthesises, copies
  * F and the peak map back, and synchronises.  Same arguments as rms_synth with
  * every array a host pointer.  Large cubes are processed in chunks of LOS

@@ -22,7 +22,7 @@ from ._binding import (  # noqa: F401
     RMS_NET_STEPS, rms_source_model, rms_generate, rms_net_create, rms_net_destroy, rms_net_info, rms_net_params,
     rms_propose, rms_net_grad, rms_train_step, rms_window_create, rms_window_destroy, rms_synth_window,
     rms_peakmap_learned, rms_plan_set_kernel_timing, rms_plan_kernel_times, rms_peak_outputs, rms_synth_peaks,
-    rms_selftest_wait_timeout, rms_clean_create, rms_clean_destroy, rms_clean,
+    rms_selftest_wait_timeout, rms_clean_create, rms_clean_destroy, rms_clean, rms_refine_peaks,
 )
 
 

@@ -36,7 +36,7 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
            "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout", "rms_clean_create",
-           "rms_clean_destroy", "rms_clean")
+           "rms_clean_destroy", "rms_clean", "rms_refine_peaks")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
             "rms_plan_set_kernel_timing": [P, _i32],
             "rms_synth_peaks": [P, P, P, _i64, _i32, P, P, P],
             "rms_selftest_wait_timeout": [P, _i64, P],
+            "rms_refine_peaks": [P, P, _i64, P, P, P, P],
             "rms_clean_create": [ctypes.POINTER(P), P, ctypes.c_double, P],
             "rms_clean_destroy": [P],
             "rms_clean": [P, P, _i64, ctypes.c_float, _i32, ctypes.c_float, P, P, P, P, P],
@@ -385,6 +386,15 @@ def rms_synth_peaks(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=Non
     st = load().rms_synth_peaks(plan, _dptr(Q, torch.float32, "Q"), _dptr(U, torch.float32, "U"), int(nlos),
                                 _layout(layout), _dptr(F_out, None, "F_out"), ctypes.byref(out), _stream(stream))
     _check(st, "rms_synth_peaks")
+
+
+def rms_refine_peaks(plan: int, F, nlos: int, peak_idx, phi_ref=None, abs_ref=None, stream=None):
+    """Parabolic sub-grid refinement of the peak (include/rms.h)."""
+    import torch
+    st = load().rms_refine_peaks(plan, _dptr(F, None, "F"), int(nlos), _dptr(peak_idx, torch.int32, "peak_idx"),
+                                 _dptr(phi_ref, torch.float32, "phi_ref"), _dptr(abs_ref, torch.float32, "abs_ref"),
+                                 _stream(stream))
+    _check(st, "rms_refine_peaks")
 
 
 def rms_selftest_wait_timeout(plan: int, limit_ns: int) -> int:

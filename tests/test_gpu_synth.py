@@ -386,6 +386,85 @@ def test_peak_outputs_need_tensor_path(rms, inputs):
         assert e.value.status == rms.RMS_ERR_UNSUPPORTED
 
 
+# ------------------------------------------------------------------- sub-grid peak refinement
+@pytest.mark.parametrize("path", ["fp32_table", "bf16x3", "fp16x3", "bf16"])
+def test_refine_peaks(rms, inputs, oracle_mod, path):
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = axes(inputs, cfg)
+    n = 2500
+    Q, U = inputs.make_cube(cfg, 5151, n)
+    dev = torch.device("cuda")
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        q = torch.from_numpy(inputs.to_layout(Q, "chan")).to(dev)
+        u = torch.from_numpy(inputs.to_layout(U, "chan")).to(dev)
+        F = torch.empty(n, cfg.nphi, 2, device=dev)
+        pidx = torch.empty(n, dtype=torch.int32, device=dev)
+        plan.synth(q, u, n, "chan", F, pidx, None, None)
+        phr, abr = torch.full((n,), -7.0, device=dev), torch.full((n,), -7.0, device=dev)
+        rms.rms_refine_peaks(plan.handle, F, n, pidx, phr, abr)
+        plan.sync()
+        Fg, ig, phr, abr = F.cpu().numpy(), pidx.cpu().numpy(), phr.cpu().numpy(), abr.cpu().numpy()
+    r = np.arange(n)
+    h = phi[1] - phi[0]
+    # properties of the GPU's own result: within the neighbours, at least the sampled height
+    ag = np.hypot(Fg[r, ig, 0].astype(np.float64), Fg[r, ig, 1].astype(np.float64))
+    lo, hi = phi[np.maximum(ig - 1, 0)], phi[np.minimum(ig + 1, cfg.nphi - 1)]
+    assert np.all((phr >= lo - 1e-5) & (phr <= hi + 1e-5))
+    assert np.all(abr >= ag * (1 - 1e-6))
+    # parity with the oracle's refinement of its own FP64 spectra, where the peak samples agree
+    op = oracle_mod.plan(freq, "freq", w)
+    Fo = oracle_mod.synth(Q, U, op, phi)
+    io, _ = oracle_mod.peak(Fo)
+    pro, aro = oracle_mod.refine_peak(Fo, phi, io)
+    same = ig == io
+    assert same.mean() > (0.95 if path == "bf16" else 0.98)
+    # per-LOS |F| error bound: the path's tolerance; plain BF16's per-LOS tail reaches 3.5e-3
+    eps = (4e-3 if path == "bf16" else gh.TOL[path]) * np.abs(Fo).max(axis=1)
+    # curvature a of the oracle's parabola: y0 - 2 y1 + y2 = 2 a h^2 on the uniform grid;
+    # |F| errors of eps move the vertex by at most 2.5 eps / (h |a|) and the height by about 4 eps
+    yo = np.abs(Fo)
+    k = np.clip(io, 1, cfg.nphi - 2)
+    a = (yo[r, k - 1] - 2 * yo[r, k] + yo[r, k + 1]) / (2 * h * h)
+    inner = same & (io > 0) & (io < cfg.nphi - 1) & (a < 0)
+    tol_phi = 2.5 * eps / (h * np.abs(np.where(a < 0, a, -1e-30))) + 4e-6 * np.abs(phi).max()
+    tol_abs = 4 * eps + 1e-6 * yo.max(axis=1)
+    assert inner.sum() > 0.9 * n
+    dphi, dabs = np.abs(phr - pro), np.abs(abr - aro)
+    assert np.all(dphi[inner] <= tol_phi[inner]), float((dphi / tol_phi)[inner].max())
+    assert np.all(dabs[same] <= tol_abs[same]), float((dabs / tol_abs)[same].max())
+
+
+def test_refine_peaks_edge_cases(rms, inputs):
+    cfg = inputs.CONFIGS["tiny"]
+    freq, w, phi = axes(inputs, cfg)
+    N = cfg.nphi
+    rows = np.full((5, N), 0.25)
+    rows[0, 0] = 3.0                                  # peak at the first sample
+    rows[1, N - 1] = 3.0                              # peak at the last sample
+    rows[2, 10:13] = [1.0, 0.5, 1.0]                  # k = 11 with a convex neighbourhood
+    rows[3, 20:23] = [1.0, 2.0, 1.5]                  # interior peak
+    F = np.stack([rows, np.zeros_like(rows)], axis=-1).astype(np.float32)
+    idx = np.array([0, N - 1, 11, 21, -1], dtype=np.int32)
+    dev = torch.device("cuda")
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        Fd, idd = torch.from_numpy(F).to(dev), torch.from_numpy(idx).to(dev)
+        phr, abr = torch.zeros(5, device=dev), torch.zeros(5, device=dev)
+        rms.rms_refine_peaks(plan.handle, Fd, 5, idd, phr, abr)
+        rms.rms_refine_peaks(plan.handle, Fd, 0, idd, phr, abr)          # empty: no-op
+        with pytest.raises(rms.RmsError) as e:
+            rms.rms_refine_peaks(plan.handle, Fd, -1, idd, phr, abr)
+        assert e.value.status == rms.RMS_ERR_INVALID_ARG
+        plan.sync()
+        phr, abr = phr.cpu().numpy(), abr.cpu().numpy()
+    np.testing.assert_array_equal(phr[:3], phi[idx[:3]].astype(np.float32))
+    np.testing.assert_array_equal(abr[:3], F[np.arange(3), idx[:3], 0])
+    h = phi[1] - phi[0]
+    delta = (1.0 - 1.5) / (2 * (1.0 - 4.0 + 1.5))                       # uniform-grid vertex offset
+    assert abs(phr[3] - (phi[21] + delta * h)) < 1e-5
+    assert abs(abr[3] - (2.0 - 0.25 * (1.0 - 1.5) * delta)) < 1e-6
+    assert np.isnan(phr[4]) and np.isnan(abr[4])
+
+
 # ------------------------------------------------------------------- failure detection
 def test_bounded_wait_gives_up_and_reports(rms, inputs):
     """A wait that cannot complete gives up after its limit, the plan reports
