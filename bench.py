@@ -318,6 +318,27 @@ def run_ours(args):
                 "algorithmic": "8 flop per (LOS, active channel, phi) (complex MAC); %d tensor products issued "
                                "per flop; achieved = algorithmic flop per launch / the contraction kernel's "
                                "CUDA-event duration" % terms}
+    elif args.path == "fp32_czt":
+        # FFT synthesis: algorithmic work counted the usual way for FFTs, 5 M log2 M flop per
+        # complex length-M transform (two per LOS), 6 flop per complex product (the spectrum
+        # times H, and the pre- and post-chirps); bytes are the cube in and F out
+        props = torch.cuda.get_device_properties(dev)
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = props.multi_processor_count * 128 * 2 * clk_mhz * 1e6 / 1e12
+        M = 1024
+        while M < cfg.nchan + cfg.nphi - 1:
+            M *= 2
+        fft_flops = L * (2 * 5.0 * M * np.log2(M) + 6.0 * M + 6.0 * (nact + cfg.nphi))
+        achieved = fft_flops / (avg_launch_ms * 1e-3) / 1e12
+        hbm_peak = peaks.get("hbm_gbs") or 6800.0
+        hbm_gbs = hbm_bytes / (avg_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": "czt_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock", "fft_length": M,
+                "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
+                "algorithmic": "per LOS 2 x 5 M log2 M + 6 M + 6 (active channels + nphi) flop; "
+                               "achieved = that / the kernel's CUDA-event duration"}
     else:
         props = torch.cuda.get_device_properties(dev)
         clk_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -370,11 +391,18 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_paths:
         paths = {}
-        for p in ("fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3"):
+        for p in ("fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3", "fp32_czt"):
             if p == args.path:
                 paths[p] = {"value": value, "ms_per_step": tmax / args.steps}
                 continue
-            with rms.Plan(freq, phi, p, weights=w, device=local) as pl:
+            try:
+                pl = rms.Plan(freq, phi, p, weights=w, device=local)
+            except rms.RmsError as e:
+                if e.status != rms.RMS_ERR_UNSUPPORTED:
+                    raise
+                paths[p] = {"unsupported": "channels not uniform in lambda^2, or nchan + nphi - 1 > 2048"}
+                continue
+            with pl:
                 n = 5 if p.startswith("fp32") else 50
 
                 def st2(pl=pl):

@@ -69,8 +69,22 @@ enum {
     RMS_FP32_SIMT_TABLE = 1,   /* FP32 CUDA cores, FP32 phase table built in FP64 */
     RMS_BF16 = 2,              /* tcgen05 tensor cores, one BF16 product, FP32 accumulate */
     RMS_BF16X3 = 3,            /* tcgen05, split BF16 hi+lo: hi*hi + hi*lo + lo*hi */
-    RMS_FP16X3 = 4             /* tcgen05, split FP16 hi+lo with per-LOS power-of-2 data scaling */
+    RMS_FP16X3 = 4,            /* tcgen05, split FP16 hi+lo with per-LOS power-of-2 data scaling */
+    RMS_FP32_CHIRPZ = 5        /* FP32 FFTs (chirp-z), exact for channels uniform in lambda^2 */
 };
+
+/*
+ * RMS_FP32_CHIRPZ evaluates Eq. Fsum with FFTs (Sec. 4 names FFTs as the route to
+ * further speed).  With x_j = lambda_j^2 - lambda_0^2 = x_0 + j D (every channel,
+ * flagged ones included) and phi_k = phi_0 + k d, 2 j k = j^2 + k^2 - (k - j)^2
+ * turns the sum into a convolution, which FFTs of length M (a power of two,
+ * 1024 <= M, nchan + nphi - 1 <= M <= 2048) compute exactly up to FP32
+ * rounding:
+ *     F_k = K e^{-i (2 phi_0 x_0 + 2 d x_0 k + d D k^2)} sum_j w_j P_j e^{-i (2 phi_0 D j + d D j^2)} e^{i d D (k - j)^2}.
+ * rms_plan_create returns RMS_ERR_UNSUPPORTED for this precision unless both
+ * axes are uniform -- each model's largest deviation times the other axis'
+ * largest |value| moves no phase by more than 1e-8 rad -- and M <= 2048.
+ */
 
 /*
  * Create a plan for one channel set and one phi grid (Sec. 2.3: K, 2 phi and
@@ -86,14 +100,15 @@ enum {
  *            the sum (NaN there is harmless).  Must be finite, >= 0, sum > 0.
  *  phi       host, [nphi] doubles, Faraday depths; any finite values, any order.
  *  nphi      1 .. 1048576.
- *  precision one of RMS_FP32_SIMT_FLY .. RMS_FP16X3.
+ *  precision one of RMS_FP32_SIMT_FLY .. RMS_FP32_CHIRPZ.
  *  device    CUDA device ordinal the plan lives on.
  *
  * Builds on the device: the FP64 phase matrix / table for the chosen precision
  * and the RMSF.  Synchronises the device before returning.
  * Returns RMS_ERR_INVALID_ARG for any invalid argument above, RMS_ERR_OOM when
- * an allocation fails, RMS_ERR_UNSUPPORTED for a tensor-core precision on a
- * device that is not compute capability 10.3, RMS_ERR_CUDA otherwise.
+ * an allocation fails, RMS_ERR_UNSUPPORTED on a device that is not compute
+ * capability 10.3 or for RMS_FP32_CHIRPZ on axes it cannot take, RMS_ERR_CUDA
+ * otherwise.
  */
 rms_status rms_plan_create(rms_plan_t *plan, const double *axis, int32_t nchan, int32_t axis_kind,
                            const double *weights, const double *phi, int32_t nphi,
@@ -152,8 +167,8 @@ rms_status rms_synth(rms_plan_t plan, const float *Q, const float *U, int64_t nl
  *                   [0, pi): the angle of the Sec. 2.2 relation (printed garbled
  *                   there; for a Faraday-thin source on the grid it is the
  *                   source's intrinsic chi0).  NaN where peak_idx = -1.
- * q_peak, u_peak and chi0 need a tensor-core precision (RMS_ERR_UNSUPPORTED for
- * the FP32 precisions).  RMS_ERR_INVALID_ARG for a NULL `out`.
+ * q_peak, u_peak and chi0 need a tensor-core precision or RMS_FP32_CHIRPZ
+ * (RMS_ERR_UNSUPPORTED for the FP32 SIMT precisions).  RMS_ERR_INVALID_ARG for a NULL `out`.
  */
 typedef struct {
     int32_t *peak_idx;

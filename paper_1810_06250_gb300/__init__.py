@@ -11,7 +11,7 @@ from __future__ import annotations
 from ._binding import (  # noqa: F401
     EXPORTS, LAYOUTS, PRECISIONS, RmsError,
     RMS_AXIS_FREQ_HZ, RMS_AXIS_LAMBDA2, RMS_BF16, RMS_BF16X3, RMS_CHAN_MAJOR, RMS_ERR_CUDA,
-    RMS_ERR_INVALID_ARG, RMS_ERR_OOM, RMS_ERR_TIMEOUT, RMS_ERR_UNSUPPORTED, RMS_FP16X3,
+    RMS_ERR_INVALID_ARG, RMS_ERR_OOM, RMS_ERR_TIMEOUT, RMS_ERR_UNSUPPORTED, RMS_FP16X3, RMS_FP32_CHIRPZ,
     RMS_FP32_SIMT_FLY, RMS_FP32_SIMT_TABLE, RMS_GET_ACTIVE, RMS_GET_B_HI, RMS_GET_B_LO,
     RMS_GET_LAMBDA2, RMS_GET_RMSF64, RMS_GET_TABLE, RMS_INFO_DEVICE, RMS_INFO_KPAD,
     RMS_INFO_NCHAN, RMS_INFO_NCHAN_ACTIVE, RMS_INFO_NPAD, RMS_INFO_NPHI, RMS_INFO_PRECISION,

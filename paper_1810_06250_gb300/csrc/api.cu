@@ -60,6 +60,7 @@ void free_plan(rms_plan_s *p)
     cudaFree(p->d_bhi);
     cudaFree(p->d_blo);
     cudaFree(p->d_R64);
+    cudaFree(p->d_czt);
     cudaFree(p->d_dl2_all);
     cudaFree(p->d_lambda2_all);
     cudaFree(p->d_w_all);
@@ -186,7 +187,7 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
     *out = nullptr;
     if (!axis || !phi || nchan < 1 || nchan > 65536 || nphi < 1 || nphi > (1 << 20)) return RMS_ERR_INVALID_ARG;
     if (axis_kind != RMS_AXIS_LAMBDA2 && axis_kind != RMS_AXIS_FREQ_HZ) return RMS_ERR_INVALID_ARG;
-    if (precision < RMS_FP32_SIMT_FLY || precision > RMS_FP16X3) return RMS_ERR_INVALID_ARG;
+    if (precision < RMS_FP32_SIMT_FLY || precision > RMS_FP32_CHIRPZ) return RMS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return RMS_ERR_CUDA;
     if (device < 0 || device >= ndev) return RMS_ERR_INVALID_ARG;
@@ -284,6 +285,12 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
     if (precision == RMS_FP32_SIMT_TABLE) {
         RMS_TRY(dalloc(&p->d_table, (size_t)p->nact * nphi));
         RMS_TRY(launch_phase_table(*p, 0));
+    } else if (precision == RMS_FP32_CHIRPZ) {
+        const rms_status cst = czt_plan_build(p);
+        if (cst != RMS_OK) {
+            free_plan(p);
+            return cst;
+        }
     } else if (is_tensor(precision)) {
         const int N = 2 * nphi;
         // RMS_MAX_TILE_N (16..208, multiple of 16) in the environment lowers the phase
@@ -430,6 +437,9 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
     case RMS_FP32_SIMT_TABLE:
         e = launch_simt(*p, p->precision == RMS_FP32_SIMT_FLY, Q, U, nlos, layout, F, pidx, pabs, pphi, s);
         break;
+    case RMS_FP32_CHIRPZ:
+        e = launch_czt(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, x.q, x.u, x.chi, s);
+        break;
     case RMS_BF16:
     case RMS_BF16X3:
     case RMS_FP16X3: {
@@ -501,7 +511,8 @@ rms_status rms_synth_peaks(rms_plan_t p, const float *Q, const float *U, int64_t
     rms_status st = check_synth_args(p, Q, U, nlos, layout, F_out);
     if (st != RMS_OK) return st;
     if (!out) return RMS_ERR_INVALID_ARG;
-    if (!is_tensor(p->precision) && (out->q_peak || out->u_peak || out->chi0)) return RMS_ERR_UNSUPPORTED;
+    if (!is_tensor(p->precision) && p->precision != RMS_FP32_CHIRPZ && (out->q_peak || out->u_peak || out->chi0))
+        return RMS_ERR_UNSUPPORTED;
     if (*p->h_err) return RMS_ERR_TIMEOUT;
     if (nlos == 0 ||
         (!F_out && !out->peak_idx && !out->peak_abs && !out->phi_peak && !out->q_peak && !out->u_peak && !out->chi0))

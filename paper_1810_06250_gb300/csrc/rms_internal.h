@@ -39,6 +39,8 @@ struct rms_plan_s {
     uint16_t *d_bhi = nullptr;     // [npad][kpad] tensor-core phase matrix, high part
     uint16_t *d_blo = nullptr;     // [npad][kpad] low part
     double *d_R64 = nullptr;       // [nphi][2]
+    float2 *d_czt = nullptr;       // chirp-z constants: H [M], twiddles [2 M], g [nchan], v [nphi]
+    int32_t czt_M = 0;             // chirp-z FFT length
     int32_t kpad = 0, npad = 0, tile_n = 0, ntiles_n = 0, tile_n_last = 0, kblocks = 0;
     CUtensorMap tmap_bhi;   // CUtensorMap is 64-byte aligned by its own declaration
     CUtensorMap tmap_blo;
@@ -94,6 +96,9 @@ cudaError_t launch_rmsf(const rms_plan_s &p, const double *d_phi, int32_t n, dou
 cudaError_t launch_simt(const rms_plan_s &p, bool fly, const float *Q, const float *U, int64_t nlos,
                         int layout, float *F, int32_t *pidx, float *pabs, float *pphi,
                         cudaStream_t s);
+rms_status czt_plan_build(rms_plan_s *p);
+cudaError_t launch_czt(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout, float *F,
+                       int32_t *pidx, float *pabs, float *pphi, float *pq, float *pu, float *pchi, cudaStream_t s);
 
 // umma.cu
 cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos,

@@ -109,13 +109,23 @@ CONFIGS = {
                            phi0=(-300.0, 300.0), slab_prob=0.5, slab_w=10.0, sigma=0.005),
     # learned-proposal workload: 2048^2 LOS on the LOFAR band and grid, SNR 5-100,
     # thin components and Burn slabs mixed as on the LOFAR cube
+    # the LOFAR cube's shape and sources with channels uniform in lambda^2 over the same
+    # band (lambda^2 from that of 178 MHz to that of 115 MHz): the case FFT synthesis takes
+    "lofar_ul2": CubeConfig("lofar_ul2", 512 * 512, 400, 115e6, 178e6, 401, -100.0, 100.0, seed=1008,
+                            flag_frac=0.10, slab_prob=0.5, slab_w=10.0, sigma=0.005,
+                            extra={"lambda2_uniform": True}),
     "learned": CubeConfig("learned", 2048 * 2048, 400, 115e6, 178e6, 401, -100.0, 100.0, seed=1005,
                           flag_frac=0.10, slab_prob=0.5, slab_w=10.0, snr=(5.0, 100.0)),
 }
 
 
 def frequencies(cfg: CubeConfig) -> np.ndarray:
-    """Channel centres, inclusive linspace(nu0, nu1, nchan) in Hz."""
+    """Channel centres in Hz: inclusive linspace(nu0, nu1, nchan), or, for a config with
+    extra["lambda2_uniform"], the frequencies whose lambda^2 = (c / nu)^2 are an inclusive
+    linspace from lambda^2(nu0) to lambda^2(nu1)."""
+    if cfg.extra.get("lambda2_uniform"):
+        l2 = np.linspace((C_LIGHT / cfg.nu0) ** 2, (C_LIGHT / cfg.nu1) ** 2, cfg.nchan)
+        return C_LIGHT / np.sqrt(l2)
     return np.linspace(cfg.nu0, cfg.nu1, cfg.nchan)
 
 
