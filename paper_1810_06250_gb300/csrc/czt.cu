@@ -167,7 +167,10 @@ __device__ __forceinline__ void stage_issue(const CztParams &P, float *st, int64
 // PF: the block copies the next W LOS into its shared stage with
 // cp.async while its warps transform the current ones (the loads' latency is
 // hidden behind the FFTs); without PF each warp loads its inputs directly.
-template <int R, bool PF>
+// HALF: nchan <= M / 2 and nphi <= M / 2, so only the first R / 2 registers
+// hold inputs and only the first R / 2 hold wanted outputs: the others are
+// compile-time zeros or dead, and the compiler drops the work on them.
+template <int R, bool PF, bool HALF>
 __global__ void __launch_bounds__(32 * Warps<R>::value, 1) czt_kernel(const CztParams P)
 {
     constexpr int M = 32 * R, r = R / 32, W = Warps<R>::value;
@@ -214,6 +217,10 @@ __global__ void __launch_bounds__(32 * Warps<R>::value, 1) czt_kernel(const CztP
         }
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1) {
+            if (HALF && n1 >= R / 2) {
+                x[n1] = make_float2(0.f, 0.f);
+                continue;
+            }
             const int j = 32 * n1 + lane;
             float2 a = make_float2(0.f, 0.f);
             if (j < P.nchan && l < P.nlos) {
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(32 * Warps<R>::value, 1) czt_kernel(const CztP
         float bm = -1.f, bre = 0.f, bim = 0.f;
         int bi = INT_MAX;
 #pragma unroll
-        for (int nb = 0; nb < R; ++nb) {
+        for (int nb = 0; nb < (HALF ? R / 2 : R); ++nb) {
             const int k = lane + 32 * nb;
             if (k < P.nphi) {
                 const float2 f = cmul(x[nb], sV[k]);
@@ -443,7 +450,13 @@ cudaError_t launch_czt(const rms_plan_s &p, const float *Q, const float *U, int6
         return err;
     };
     cudaError_t e;
-    if (R == 32) e = pf ? go(czt_kernel<32, true>) : go(czt_kernel<32, false>);
-    else e = pf ? go(czt_kernel<64, true>) : go(czt_kernel<64, false>);
+    const bool half = 2 * p.nchan <= M && 2 * p.nphi <= M;
+    if (R == 32) {
+        if (half) e = pf ? go(czt_kernel<32, true, true>) : go(czt_kernel<32, false, true>);
+        else e = pf ? go(czt_kernel<32, true, false>) : go(czt_kernel<32, false, false>);
+    } else {
+        if (half) e = pf ? go(czt_kernel<64, true, true>) : go(czt_kernel<64, false, true>);
+        else e = pf ? go(czt_kernel<64, true, false>) : go(czt_kernel<64, false, false>);
+    }
     return e == cudaSuccess ? cudaGetLastError() : e;
 }

@@ -60,11 +60,15 @@ def run(rms, inputs, cfg, Q, U, layout, n, extras=False):
     return F.cpu().numpy(), [t.cpu().numpy() for t in out], l0
 
 
-# (config, LOS, overrides): FFT length 1024 for tiny and LOFAR shapes, 2048 for
-# 800 x 1001; 1000 channels x 25 phi has no room for the input stage (the
-# kernel variant that loads directly); LOS counts that leave ragged warps and blocks
+# (config, LOS, overrides), covering every kernel variant: FFT length 1024 for
+# tiny and LOFAR shapes, 2048 for 800 x 1001 and 1200 x 401; half-length inputs
+# and outputs (nchan, nphi <= M / 2) or not (520 x 100, 1000 x 25, 1200 x 401);
+# with the input stage or without it (1000 x 25 and the 2048-point cases); LOS
+# counts that leave ragged warps and blocks
 CASES = [("tiny", 256, {}), ("tiny", 13, {}), ("lofar", 2999, {}), ("precision", 1031, {}),
-         ("lofar", 517, {"nchan": 1000, "nphi": 25, "phi_min": -12.0, "phi_max": 12.0})]
+         ("lofar", 301, {"nchan": 520, "nphi": 100, "phi_min": -50.0, "phi_max": 50.0}),
+         ("lofar", 517, {"nchan": 1000, "nphi": 25, "phi_min": -12.0, "phi_max": 12.0}),
+         ("lofar", 203, {"nchan": 1200})]
 
 
 @pytest.mark.parametrize("layout", ["chan", "los"])
