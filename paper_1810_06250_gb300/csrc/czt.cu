@@ -14,8 +14,8 @@
 //
 // One warp transforms one line of sight; M = 32 R (R = 32 or 64).  Element n of
 // a length-M sequence is held by lane n % 32 in register n / 32.  Forward:
-// an R-point DFT per lane in registers, a twiddle, a transpose through shared
-// memory, then 32-point DFTs per lane (the four-step FFT); the product with H;
+// an R-point DFT per lane in registers (radix 4), a twiddle, a transpose through
+// shared memory, then 32-point DFTs per lane (the four-step FFT); the product with H;
 // the inverse runs the same steps backwards, so its output comes back in the
 // input's layout and the warp writes 32 consecutive phi per store.
 #include <math.h>
@@ -42,8 +42,8 @@ struct Warps {
 constexpr int kLd = 33;
 __device__ __forceinline__ int tidx(int row, int col) { return row * kLd + col; }
 
-// W_64^m = exp(-2 pi i m / 64), m < 32: the twiddles of every in-register DFT
-__constant__ float2 c_w64[32];
+// W_64^m = exp(-2 pi i m / 64), m < 64: the twiddles of every in-register DFT
+__constant__ float2 c_w64[64];
 
 struct CztParams {
     const float *Q, *U;
@@ -61,14 +61,12 @@ struct CztParams {
     float *pabs, *pphi, *pq, *pu, *pchi;
 };
 
-__host__ __device__ constexpr int bitrev(int i, int n)
+// Output position of frequency k after the radix-4 (and, for N = 32, final
+// radix-2) decimation-in-frequency stages: k = m1 + 4 m2 + 16 m3 sits at
+// (N / 4) m1 + (N / 16) m2 + m3.
+__host__ __device__ constexpr int digitrev(int k, int n)
 {
-    int r = 0;
-    for (int b = 1; b < n; b <<= 1) {
-        r = (r << 1) | (i & 1);
-        i >>= 1;
-    }
-    return r;
+    return (n / 4) * (k % 4) + (n / 16) * ((k / 4) % 4) + k / 16;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -86,32 +84,50 @@ template <bool INV>
 __device__ __forceinline__ float2 twiddle64(float2 d, int m)
 {
     if (m == 0) return d;
-    if (m == 16) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);   // -i or +i
+    if (m == 32) return make_float2(-d.x, -d.y);
+    if (m == 16) return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);   // -i, or +i inverse
+    if (m == 48) return INV ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);   // +i, or -i inverse
     return INV ? cmulc(d, c_w64[m]) : cmul(d, c_w64[m]);
 }
 
 // In-register N-point DFT, N = 32 or 64, natural order in and out:
-// v_k <- sum_n v_n W_N^(+-nk).  Radix-2 decimation in frequency, then the
-// bit-reversal permutation, which is a renaming of registers once unrolled.
+// v_k <- sum_n v_n W_N^(+-nk).  Radix-4 decimation in frequency (a last radix-2
+// stage for N = 32), then the digit-reversal permutation, which is a renaming
+// of registers once unrolled.  Per radix-4 butterfly on a span of L points:
+//     t0 = a + c, t1 = a - c, t2 = b + d, t3 = -+i (b - d)
+//     outputs t0 + t2, (t1 + t3) W_L^j, (t0 - t2) W_L^2j, (t1 - t3) W_L^3j.
 template <int N, bool INV>
 __device__ __forceinline__ void dft_reg(float2 (&v)[N])
 {
 #pragma unroll
-    for (int half = N / 2; half >= 1; half >>= 1) {
+    for (int L = N; L >= 4; L /= 4) {
+        const int q = L / 4;
 #pragma unroll
-        for (int base = 0; base < N; base += 2 * half) {
+        for (int base = 0; base < N; base += L) {
 #pragma unroll
-            for (int j = 0; j < half; ++j) {
-                const float2 a = v[base + j], b = v[base + j + half];
-                v[base + j] = make_float2(a.x + b.x, a.y + b.y);
-                // W_(2 half)^j = W_64^(j 32 / half)
-                v[base + j + half] = twiddle64<INV>(make_float2(a.x - b.x, a.y - b.y), j * (32 / half));
+            for (int j = 0; j < q; ++j) {
+                const float2 a = v[base + j], b = v[base + j + q], c = v[base + j + 2 * q], d = v[base + j + 3 * q];
+                const float2 t0 = make_float2(a.x + c.x, a.y + c.y), t1 = make_float2(a.x - c.x, a.y - c.y);
+                const float2 t2 = make_float2(b.x + d.x, b.y + d.y);
+                const float2 t3 = INV ? make_float2(d.y - b.y, b.x - d.x) : make_float2(b.y - d.y, d.x - b.x);
+                v[base + j] = make_float2(t0.x + t2.x, t0.y + t2.y);
+                v[base + j + q] = twiddle64<INV>(make_float2(t1.x + t3.x, t1.y + t3.y), j * 64 / L);
+                v[base + j + 2 * q] = twiddle64<INV>(make_float2(t0.x - t2.x, t0.y - t2.y), 2 * j * 64 / L);
+                v[base + j + 3 * q] = twiddle64<INV>(make_float2(t1.x - t3.x, t1.y - t3.y), 3 * j * 64 / L);
             }
+        }
+    }
+    if (N == 32) {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const float2 a = v[i], b = v[i + 1];
+            v[i] = make_float2(a.x + b.x, a.y + b.y);
+            v[i + 1] = make_float2(a.x - b.x, a.y - b.y);
         }
     }
     float2 t[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) t[i] = v[bitrev(i, N)];
+    for (int i = 0; i < N; ++i) t[i] = v[digitrev(i, N)];
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = t[i];
 }
@@ -385,8 +401,8 @@ rms_status czt_plan_build(rms_plan_s *p)
                 const std::complex<double> t = W[(n * (ln + 32 * s)) % M];
                 tw[M + (s * 32 + n) * 32 + ln] = make_float2((float)t.real(), (float)t.imag());
             }
-    float2 w64[32];
-    for (int m = 0; m < 32; ++m) {
+    float2 w64[64];
+    for (int m = 0; m < 64; ++m) {
         const std::complex<double> t = expi(-two_pi * m / 64.0);
         w64[m] = make_float2((float)t.real(), (float)t.imag());
     }
