@@ -553,6 +553,17 @@ def run_learned(args):
             def bf16_step():
                 p1.synth(Q, U, L, args.layout, None, fidx, fabs, fphi, stream)
             t_bf16, _ = time_steps(bf16_step, stream, max(3, args.steps // 2), 2, torch)
+        # the full grid at the window's resolution (step D/2 over the same range: the
+        # fine grid every window is cut from), same precision
+        phi_fine = cfg.phi_min + 0.5 * (phi[1] - phi[0]) * np.arange(2 * cfg.nphi - 1)
+        gidx = torch.empty(L, dtype=torch.int32, device=dev)
+        gphi = torch.empty(L, device=dev)
+        gabs = torch.empty(L, device=dev)
+        with rms.Plan(freq, phi_fine, args.path, weights=w, device=local) as p2:
+            def fine_step():
+                p2.synth(Q, U, L, args.layout, None, gidx, gabs, gphi, stream)
+            t_fine, _ = time_steps(fine_step, stream, max(3, args.steps // 2), 2, torch)
+            fine_step()
         full_step()
         learned_step()
     torch.cuda.synchronize()
@@ -560,7 +571,11 @@ def run_learned(args):
     ms_learn = t_learn / args.steps
     ms_full = t_full / max(3, args.steps // 2)
     ms_bf16 = t_bf16 / max(3, args.steps // 2)
+    ms_fine = t_fine / max(3, args.steps // 2)
     agree = float(np.mean(np.abs(php.cpu().numpy().astype(np.float64) - fphi.cpu().numpy()) <= 0.5 * (1 + 1e-6)))
+    dfine = np.abs(php.cpu().numpy().astype(np.float64) - gphi.cpu().numpy())
+    agree_fine_point = float(np.mean(dfine <= 1e-3))
+    agree_fine = float(np.mean(dfine <= 0.5 * (1 + 1e-6)))
     fbr = float(fb.cpu().numpy().mean())
     from paper_1810_06250_gb300.dist import throughput
     value, tmax = throughput(units, args.steps, t_learn, world, dev)
@@ -582,8 +597,11 @@ def run_learned(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "learned": {"speedup_vs_full_grid_same_precision": ms_full / ms_learn,
                         "speedup_vs_full_grid_bf16": ms_bf16 / ms_learn,
+                        "speedup_vs_fine_full_grid_same_precision": ms_fine / ms_learn,
                         "ms_learned": ms_learn, "ms_full_grid": ms_full, "ms_full_grid_bf16": ms_bf16,
-                        "agreement": agree, "fallback_frac": fbr, "tau": tau, "val_fallback_frac": cal["fallback_frac"],
+                        "ms_fine_full_grid": ms_fine, "fine_grid_nphi": int(len(phi_fine)),
+                        "agreement": agree, "agreement_fine_grid": agree_fine,
+                        "same_fine_point": agree_fine_point, "fallback_frac": fbr, "tau": tau, "val_fallback_frac": cal["fallback_frac"],
                         "train_loss": hist, "train_s": train_s, "n_train": args.n_train, "epochs": args.epochs,
                         "hidden": args.hidden,
                         "params": int(net.nparams), "flop_per_los": 2 * (net.nparams - args.hidden - cfg.nphi)},
