@@ -68,7 +68,8 @@ def run(rms, inputs, cfg, Q, U, layout, n, extras=False):
 CASES = [("tiny", 256, {}), ("tiny", 13, {}), ("lofar", 2999, {}), ("precision", 1031, {}),
          ("lofar", 301, {"nchan": 520, "nphi": 100, "phi_min": -50.0, "phi_max": 50.0}),
          ("lofar", 517, {"nchan": 1000, "nphi": 25, "phi_min": -12.0, "phi_max": 12.0}),
-         ("lofar", 203, {"nchan": 1200})]
+         ("lofar", 203, {"nchan": 1200}),
+         ("lofar", 64, {"nchan": 1048, "nphi": 1001, "phi_min": -250.0, "phi_max": 250.0})]   # M = 2048 exactly
 
 
 @pytest.mark.parametrize("layout", ["chan", "los"])
@@ -104,6 +105,28 @@ def test_czt_flagged_nan_and_thin_source(rms, inputs, oracle_mod):
     Fo = oracle_mod.synth(Qz, Uz, oracle_mod.plan(freq, "freq", w), phi)
     ok, info = gh.gate(PATH, F[..., 0] + 1j * F[..., 1], Fo)
     assert ok, info
+
+
+def test_czt_nan_and_zero_lines_of_sight(rms, inputs, oracle_mod):
+    # a NaN in an active channel reaches every output of its LOS (the FFT mixes all
+    # channels), so that LOS has no peak; an all-zero LOS peaks at index 0 (a tie)
+    cfg = ul2(inputs, "lofar", nlos=40)
+    freq, w, phi = axes(inputs, cfg)
+    Q, U = inputs.make_cube(cfg, 0, 40)
+    act = np.nonzero(w)[0]
+    Q[5, act[3]] = np.nan
+    Q[9] = 0.0
+    U[9] = 0.0
+    F, (pidx, pabs, pphi), _ = run(rms, inputs, cfg, Q, U, "chan", 40)
+    assert np.all(np.isnan(F[5]))
+    assert pidx[5] == -1 and np.isnan(pabs[5]) and np.isnan(pphi[5])
+    assert np.all(F[9] == 0) and pidx[9] == 0 and pabs[9] == 0
+    good = np.ones(40, dtype=bool)
+    good[5] = False
+    Fo = oracle_mod.synth(Q[good], U[good], oracle_mod.plan(freq, "freq", w), phi)
+    ok, info = gh.gate(PATH, F[good, :, 0] + 1j * F[good, :, 1], Fo)
+    assert ok, info
+    gh.check_peaks_self(F, pidx, pabs, pphi, phi)
 
 
 def test_czt_peak_outputs(rms, inputs, oracle_mod):
