@@ -226,6 +226,32 @@ def sample_rows(cfg, n, rng):
     return rows, np.concatenate(Qs), np.concatenate(Us)
 
 
+def oracle_sample(cfg, freq, w, phi, L, seconds):
+    """The FP64 oracle, as it stands, on all host cores over a LOS sample of about `seconds` of
+    work: the CPU baseline and the reference values of the error check."""
+    import oracle
+    from paper_1810_06250_gb300 import inputs
+    oracle.build()
+    op = oracle.plan(freq, "freq", w)
+    nact = int(np.count_nonzero(w))
+    # calibrate on enough LOS to keep every host core busy, then size the sample
+    ncal = int(min(L, 64 * max(1, oracle.num_threads())))
+    Qc, Uc = inputs.make_cube(cfg, 0, ncal)
+    t0 = time.perf_counter()
+    oracle.synth(Qc, Uc, op, phi)
+    per_los = (time.perf_counter() - t0) / ncal
+    n = int(min(L, max(256, seconds / per_los)))
+    rows, Qs, Us = sample_rows(cfg, n, np.random.default_rng(12345))
+    t0 = time.perf_counter()
+    Fo = oracle.synth(Qs, Us, op, phi)
+    dt = time.perf_counter() - t0
+    base = {"value": len(rows) * nact * cfg.nphi / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d of %d LOS in 64-LOS blocks (all %d active channels x %d phi), FP64 C oracle, OpenMP over "
+                      "LOS, %.1f s" % (len(rows), L, nact, cfg.nphi, dt)}
+    return {"rows": rows, "Fo": Fo, "peak": oracle.peak(Fo), "plan": op, "baseline": base}
+
+
 def run_ours(args):
     import dataclasses
     import torch
@@ -389,6 +415,26 @@ def run_ours(args):
                          "component_updates_per_s": Lc * mean_it * cfg.nphi / (t_cl / 3 * 1e-3)}
         del Fc, nit
 
+    # the FP64 oracle on a bounded LOS sample: the CPU baseline, and the error of every path
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(cfg, freq, w, phi, L, args.cpu_seconds)
+        sel = torch.from_numpy(cpu["rows"]).to(dev)
+
+    def error_vs_fp64(Fd, pidx_d, pabs_d):
+        Fo = cpu["Fo"]
+        if Fd is not None:
+            Fg = Fd[sel].cpu().numpy()
+            Fg = Fg[..., 0] + 1j * Fg[..., 1]
+            d = np.abs(Fg - Fo)
+            per_los = d.max(axis=1) / np.abs(Fo).max(axis=1)
+            return {"per_los_max": float(per_los.max()), "per_los_p999": float(np.quantile(per_los, 0.999)),
+                    "cube": float(d.max() / np.abs(Fo).max()), "sample_los": int(len(cpu["rows"]))}
+        oi, oa = cpu["peak"]
+        ga = pabs_d[sel].cpu().numpy()
+        return {"peak_abs_rel_max": float(np.max(np.abs(ga - oa) / np.abs(Fo).max(axis=1))),
+                "peak_idx_equal": float(np.mean(pidx_d[sel].cpu().numpy() == oi)), "sample_los": int(len(cpu["rows"]))}
+
     if rank == 0 and world == 1 and not args.no_paths:
         paths = {}
         for p in ("fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3", "fp32_czt"):
@@ -411,6 +457,9 @@ def run_ours(args):
                     tot, _ = time_steps(st2, stream, n, 2, torch)
                 pl.sync(stream)
                 paths[p] = {"value": units * n / (tot * 1e-3) / 1e9, "ms_per_step": tot / n}
+                if cpu is not None:
+                    torch.cuda.synchronize()
+                    paths[p]["error_vs_fp64"] = error_vs_fp64(F, pidx, pabs)
         line["paths"] = paths
         # restore this path's output for the error check below
         plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
@@ -438,48 +487,21 @@ def run_ours(args):
                        "how": "rms_synth_host: pinned host Q/U -> device in LOS chunks, synthesis, F and peak "
                               "map -> pinned host, copies overlapped on three streams, sync"}
 
-    if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle
-        oracle.build()
-        op = oracle.plan(freq, "freq", w)
-        # calibrate on enough LOS to keep every host core busy, then size the sample
-        ncal = int(min(L, 64 * max(1, oracle.num_threads())))
-        Qc, Uc = inputs.make_cube(cfg, 0, ncal)
-        t0 = time.perf_counter()
-        oracle.synth(Qc, Uc, op, phi)
-        per_los = (time.perf_counter() - t0) / ncal
-        n = int(min(L, max(256, args.cpu_seconds / per_los)))
-        rows, Qs, Us = sample_rows(cfg, n, np.random.default_rng(12345))
-        t0 = time.perf_counter()
-        Fo = oracle.synth(Qs, Us, op, phi)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": len(rows) * nact * cfg.nphi / dt / 1e9, "unit": UNIT,
-                                "cores": oracle.num_threads(), "kind": "oracle",
-                                "sample": "%d of %d LOS in 64-LOS blocks (all %d active channels x %d phi), FP64 C "
-                                          "oracle, OpenMP over LOS, %.1f s" % (len(rows), L, nact, cfg.nphi, dt)}
-        sel = torch.from_numpy(rows).to(dev)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu["baseline"]
         if "clean" in line:
+            import oracle
             from oracle import clean as oclean
             dphi = float(phi[1] - phi[0])
-            R2 = oracle.rmsf(op, (np.arange(2 * len(phi) - 1) - (len(phi) - 1)) * dphi)
-            k = min(len(rows), 256)
+            R2 = oracle.rmsf(cpu["plan"], (np.arange(2 * len(phi) - 1) - (len(phi) - 1)) * dphi)
+            k = min(len(cpu["rows"]), 256)
             t0 = time.perf_counter()
-            oclean.clean(Fo[:k], R2, 0.1, 1000, line["clean"]["threshold"], oracle.fwhm_measured(op), dphi)
+            oclean.clean(cpu["Fo"][:k], R2, 0.1, 1000, line["clean"]["threshold"], oracle.fwhm_measured(cpu["plan"]),
+                         dphi)
             line["clean"]["cpu_oracle_los_per_s"] = k / (time.perf_counter() - t0)
-        if F is not None:
-            Fg = F[sel].cpu().numpy()
-            Fg = Fg[..., 0] + 1j * Fg[..., 1]
-            d = np.abs(Fg - Fo)
-            per_los = d.max(axis=1) / np.abs(Fo).max(axis=1)
-            line["error_vs_fp64"] = {"per_los_max": float(per_los.max()),
-                                     "per_los_p999": float(np.quantile(per_los, 0.999)),
-                                     "cube": float(d.max() / np.abs(Fo).max()), "sample_los": int(len(rows))}
-        else:
-            oi, oa = oracle.peak(Fo)
-            ga = pabs[sel].cpu().numpy()
-            line["error_vs_fp64"] = {"peak_abs_rel_max": float(np.max(np.abs(ga - oa) / np.abs(Fo).max(axis=1))),
-                                     "peak_idx_equal": float(np.mean(pidx[sel].cpu().numpy() == oi)),
-                                     "sample_los": int(len(rows))}
+        line["error_vs_fp64"] = error_vs_fp64(F, pidx, pabs)
+        if "paths" in line:
+            line["paths"][args.path]["error_vs_fp64"] = line["error_vs_fp64"]
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
