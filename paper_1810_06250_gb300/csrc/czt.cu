@@ -1,6 +1,6 @@
 // Chirp-z synthesis: Eq. Fsum evaluated with FFTs when the channels are
-// uniform in lambda^2 and the phi grid is uniform (the paper's FFT remark in
-// Sec. 4 names this case).  With x_j = lambda_j^2 - lambda_0^2 = x_0 + j D and
+// uniform in lambda^2 and the phi grid is uniform (Sec. 4 names FFTs as the
+// route to further speed; they are exact in this case).  With x_j = lambda_j^2 - lambda_0^2 = x_0 + j D and
 // phi_k = phi_0 + k d, the phase of term (j, k) is
 //     2 phi_k x_j = 2 phi_0 x_0 + 2 phi_0 D j + 2 d x_0 k + 2 d D j k,
 // and 2 j k = j^2 + k^2 - (k - j)^2 turns the sum into a convolution:
