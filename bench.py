@@ -358,13 +358,18 @@ def run_ours(args):
         achieved = fft_flops / (avg_launch_ms * 1e-3) / 1e12
         hbm_peak = peaks.get("hbm_gbs") or 6800.0
         hbm_gbs = hbm_bytes / (avg_launch_ms * 1e-3) / 1e9
+        traffic = measured_traffic("czt.cu", "czt_lofar_ul2.md") \
+            if (args.config == "lofar_ul2" and args.layout == "chan" and args.nlos is None and not peak_only) else None
         roof = {"kernel": "czt_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": "SMs x 128 FP32 lanes x 2 x max SM clock", "fft_length": M,
                 "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
                 "algorithmic": "per LOS 2 x 5 M log2 M + 6 M + 6 (active channels + nphi) flop; "
-                               "achieved = that / the kernel's CUDA-event duration"}
+                               "achieved = that / the kernel's CUDA-event duration",
+                "note": "an FFT is mostly additions, one flop per FP32 instruction against two for an FMA, so "
+                        "the FMA-flop peak overstates what it can reach; ncu counts the issue slots instead "
+                        "(profiles/czt_lofar_ul2.md)"}
     else:
         props = torch.cuda.get_device_properties(dev)
         clk_mhz = peaks.get("sm_max_mhz", 2070.0)
