@@ -158,6 +158,85 @@ __device__ __forceinline__ void fly_store(Stage &st, const FlyOps &o, int tid)
     }
 }
 
+// Pipeline state carried from one phi tile to the next.
+struct Pipe {
+    int t;          // (phi tile, channel chunk) pair being accumulated
+    int total, nck;
+    int32_t act;    // active-channel index for the next copy
+};
+
+// One phi tile starting at p0: accumulate all channel chunks, then scale, store
+// and update the running peak.  JJ: phi pairs-of-16 of the tile that hold grid
+// points (4 for a full tile; the last, partial tile drops the columns beyond).
+template <int JJ, bool FLY, int LAYOUT>
+__device__ __forceinline__ void phi_tile(const SimtArgs &a, Stage *stage, int64_t l0, int p0, Pipe &pp, FlyOps &fo,
+                                         float (&bm)[8], int (&bi)[8])
+{
+    constexpr int NJ = 2 * JJ;
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    float re[8][NJ], im[8][NJ];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) { re[i][j] = 0.f; im[i][j] = 0.f; }
+
+    for (int ck = 0; ck < pp.nck; ++ck, ++pp.t) {
+        const int n = pp.t + 1;
+        if (n < pp.total) {
+            issue<FLY, LAYOUT>(a, stage[n & 1], l0, (n % pp.nck) * CH, (n / pp.nck) * TP, pp.act, tid);
+            if (FLY) fly_load(a, fo, (n % pp.nck) * CH, (n / pp.nck) * TP, tid);
+            if (n + 1 < pp.total) pp.act = load_active<LAYOUT>(a, ((n + 1) % pp.nck) * CH, tid);
+        }
+        cp_commit();
+        cp_wait_prev();
+        __syncthreads();
+        const Stage &st = stage[pp.t & 1];
+#pragma unroll 2
+        for (int c = 0; c < CH; ++c) {
+            float qv[8], uv[8], cv[NJ], sv[NJ];
+            load8(&st.q[c][8 * ty], qv);
+            load8(&st.u[c][8 * ty], uv);
+            // thread tx owns phi pairs 16 jj + 2 tx + {0, 1}: the 8 threads of a
+            // row read 128 contiguous bytes per vector load (no bank conflict)
+#pragma unroll
+            for (int j = 0; j < NJ; j += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(&st.cs[c][8 * j + 2 * tx]);
+                cv[j] = v.x; sv[j] = v.y; cv[j + 1] = v.z; sv[j + 1] = v.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    // (q + iu)(c - is): Re += q c + u s, Im += u c - q s  (Eqs. qPhi, uPhi)
+                    re[i][j] = fmaf(qv[i], cv[j], re[i][j]);
+                    re[i][j] = fmaf(uv[i], sv[j], re[i][j]);
+                    im[i][j] = fmaf(uv[i], cv[j], im[i][j]);
+                    im[i][j] = fmaf(-qv[i], sv[j], im[i][j]);
+                }
+        }
+        // stage n & 1 was last read before the previous trailing barrier
+        if (FLY && n < pp.total) fly_store(stage[n & 1], fo, tid);
+        __syncthreads();
+    }
+
+    // epilogue for this phi tile: scale by K, store, update the running peak
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t l = l0 + 8 * ty + i;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int k = p0 + 16 * (j >> 1) + 2 * tx + (j & 1);
+            const float fr = re[i][j] * a.scale, fi = im[i][j] * a.scale;
+            if (k < a.nphi) {
+                const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
+                if (m2 > bm[i]) { bm[i] = m2; bi[i] = k; }
+                if (a.F != nullptr && l < a.nlos)
+                    *reinterpret_cast<float2 *>(a.F + (l * a.nphi + k) * 2) = make_float2(fr, fi);
+            }
+        }
+    }
+}
+
 template <bool FLY, int LAYOUT>
 __global__ void __launch_bounds__(256, 1) simt_kernel(const SimtArgs a)
 {
@@ -166,8 +245,10 @@ __global__ void __launch_bounds__(256, 1) simt_kernel(const SimtArgs a)
 
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     const int64_t l0 = (int64_t)blockIdx.x * TL;
-    const int nck = (a.nact + CH - 1) / CH;
-    const int total = nck * ((a.nphi + TP - 1) / TP);
+    Pipe pp;
+    pp.nck = (a.nact + CH - 1) / CH;
+    pp.total = pp.nck * ((a.nphi + TP - 1) / TP);
+    pp.t = 0;
 
     float bm[8];
     int bi[8];
@@ -179,74 +260,20 @@ __global__ void __launch_bounds__(256, 1) simt_kernel(const SimtArgs a)
     FlyOps fo;
     issue<FLY, LAYOUT>(a, stage[0], l0, 0, 0, load_active<LAYOUT>(a, 0, tid), tid);
     cp_commit();
-    int32_t act = total > 1 ? load_active<LAYOUT>(a, (1 % nck) * CH, tid) : -1;
+    pp.act = pp.total > 1 ? load_active<LAYOUT>(a, (1 % pp.nck) * CH, tid) : -1;
     if (FLY) {
         fly_load(a, fo, 0, 0, tid);
         fly_store(stage[0], fo, tid);
     }
-    int t = 0;
-    for (int p0 = 0; p0 < a.nphi; p0 += TP) {
-        float re[8][8], im[8][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) { re[i][j] = 0.f; im[i][j] = 0.f; }
-
-        for (int ck = 0; ck < nck; ++ck, ++t) {
-            const int n = t + 1;
-            if (n < total) {
-                issue<FLY, LAYOUT>(a, stage[n & 1], l0, (n % nck) * CH, (n / nck) * TP, act, tid);
-                if (FLY) fly_load(a, fo, (n % nck) * CH, (n / nck) * TP, tid);
-                if (n + 1 < total) act = load_active<LAYOUT>(a, ((n + 1) % nck) * CH, tid);
-            }
-            cp_commit();
-            cp_wait_prev();
-            __syncthreads();
-            const Stage &st = stage[t & 1];
-#pragma unroll 2
-            for (int c = 0; c < CH; ++c) {
-                float qv[8], uv[8], cv[8], sv[8];
-                load8(&st.q[c][8 * ty], qv);
-                load8(&st.u[c][8 * ty], uv);
-                // thread tx owns phi pairs 16 jj + 2 tx + {0, 1}: the 8 threads of a
-                // row read 128 contiguous bytes per vector load (no bank conflict)
-#pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    const float4 v = *reinterpret_cast<const float4 *>(&st.cs[c][8 * j + 2 * tx]);
-                    cv[j] = v.x; sv[j] = v.y; cv[j + 1] = v.z; sv[j + 1] = v.w;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        // (q + iu)(c - is): Re += q c + u s, Im += u c - q s  (Eqs. qPhi, uPhi)
-                        re[i][j] = fmaf(qv[i], cv[j], re[i][j]);
-                        re[i][j] = fmaf(uv[i], sv[j], re[i][j]);
-                        im[i][j] = fmaf(uv[i], cv[j], im[i][j]);
-                        im[i][j] = fmaf(-qv[i], sv[j], im[i][j]);
-                    }
-            }
-            // stage n & 1 was last read before the previous trailing barrier
-            if (FLY && n < total) fly_store(stage[n & 1], fo, tid);
-            __syncthreads();
-        }
-
-        // epilogue for this phi tile: scale by K, store, update the running peak
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t l = l0 + 8 * ty + i;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int k = p0 + 16 * (j >> 1) + 2 * tx + (j & 1);
-                const float fr = re[i][j] * a.scale, fi = im[i][j] * a.scale;
-                if (k < a.nphi) {
-                    const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
-                    if (m2 > bm[i]) { bm[i] = m2; bi[i] = k; }
-                    if (a.F != nullptr && l < a.nlos)
-                        *reinterpret_cast<float2 *>(a.F + (l * a.nphi + k) * 2) = make_float2(fr, fi);
-                }
-            }
-        }
+    const int full = a.nphi / TP, rem = a.nphi - full * TP;
+    for (int it = 0; it < full; ++it) phi_tile<4, FLY, LAYOUT>(a, stage, l0, it * TP, pp, fo, bm, bi);
+    // the last, partial tile computes only the pairs-of-16 that hold grid points
+    switch ((rem + 15) / 16) {
+    case 1: phi_tile<1, FLY, LAYOUT>(a, stage, l0, full * TP, pp, fo, bm, bi); break;
+    case 2: phi_tile<2, FLY, LAYOUT>(a, stage, l0, full * TP, pp, fo, bm, bi); break;
+    case 3: phi_tile<3, FLY, LAYOUT>(a, stage, l0, full * TP, pp, fo, bm, bi); break;
+    case 4: phi_tile<4, FLY, LAYOUT>(a, stage, l0, full * TP, pp, fo, bm, bi); break;
+    default: break;
     }
 
     // reduce the peak over the 8 threads (tx) that share each line of sight
