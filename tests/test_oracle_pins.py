@@ -141,3 +141,16 @@ def test_refine_undefined_cases_keep_the_sample(oracle_mod):
     # both neighbours on one side of phi_k (a non-monotonic grid): the sample
     pr, ar = oracle_mod.refine_peak(np.array([[1.0, 2.0, 1.5]], dtype=np.complex128), [0.0, 1.0, 0.5], [1])
     assert pr[0] == 1.0 and ar[0] == 2.0
+
+
+# ------------------------------------------------------------------- the paper's cost example
+def test_unit_count_reproduces_the_papers_cost_example():
+    # the benchmark's unit is one (LOS, channel, phi) triple; at the paper's 15 flop per unit
+    # the WSRT-SINGS-shaped cube of Sec. 2.3 must come to its printed ~1.27 TFLOP
+    import json
+    import os
+    from paper_1810_06250_gb300.inputs import CubeConfig
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_cost.json")))
+    cfg = CubeConfig("wsrt_sings_shape", g["nlos"], g["nchan"], 1.3e9, 1.45e9, g["nphi"], -100.0, 100.0, seed=1)
+    tflop = cfg.units * g["flop_per_unit"] / 1e12
+    assert round(tflop, g["printed_digits"]) == g["tflop_printed"]
