@@ -115,6 +115,10 @@ __device__ __forceinline__ void load_kblock(const SplitParams &P, int64_t src, b
     }
 }
 
+// PAIRS: LOS-major rows with 16-byte aligned channels, two K blocks per load
+// batch (a separate instantiation: its extra registers would cost the
+// channel-major split occupancy).
+template <bool PAIRS>
 __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
 {
     const int m = threadIdx.x;
@@ -142,10 +146,10 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
         if (valid) P.rexp[row] = (int8_t)e;
     }
     float ss = 0.f;
-    uint8_t *dst = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
-    for (int kb = 0; kb < P.kblocks; ++kb, dst += 2 * kStageA) {
-        float q[16], u[16];
-        load_kblock(P, src, valid, kb, q, u);
+    uint8_t *const dst0 = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
+    // write K block kb of this row: hi and lo chunks at their swizzled places
+    auto emit = [&](int kb, const float *q, const float *u) {
+        uint8_t *dst = dst0 + (size_t)kb * (2 * kStageA);
         if (P.rscale) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) ss = fmaf(q[i], q[i], fmaf(u[i], u[i], ss));
@@ -163,6 +167,59 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
             *reinterpret_cast<uint4 *>(dst + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             if (P.mode != MODE_BF16)
                 *reinterpret_cast<uint4 *>(dst + kStageA + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    };
+    if (!PAIRS) {
+        uint8_t *dst = dst0;
+        for (int kb = 0; kb < P.kblocks; ++kb, dst += 2 * kStageA) {
+            float q[16], u[16];
+            load_kblock(P, src, valid, kb, q, u);
+            if (P.rscale) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) ss = fmaf(q[i], q[i], fmaf(u[i], u[i], ss));
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = 4 * c + j;
+                    if (P.mode == MODE_FP16X3) split_pair_fp16(q[i] * scale, u[i] * scale, hi[j], lo[j]);
+                    else split_pair_bf16(q[i], u[i], hi[j], lo[j]);
+                }
+                const uint32_t off = (uint32_t)m * kRowBytes + ((uint32_t)(c ^ sw) << 4);
+                *reinterpret_cast<uint4 *>(dst + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                if (P.mode != MODE_BF16)
+                    *reinterpret_cast<uint4 *>(dst + kStageA + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+    } else {
+        for (int kb = 0; kb < P.kblocks;) {
+            if (valid && kb + 1 < P.kblocks && (kb + 2) * kChanPerKBlock <= P.nchan) {
+                // two K blocks at once: 128 contiguous bytes of the row per array, whole lines
+                const int c0 = kb * kChanPerKBlock;
+                const uint32_t live = __ldg(P.kbmask + kb) | ((uint32_t)__ldg(P.kbmask + kb + 1) << 16);
+                const float4 *q4 = reinterpret_cast<const float4 *>(P.Q + src * P.nchan + c0);
+                const float4 *u4 = reinterpret_cast<const float4 *>(P.U + src * P.nchan + c0);
+                float q[32], u[32];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const float4 a = __ldg(q4 + v), b = __ldg(u4 + v);
+                    q[4 * v] = a.x; q[4 * v + 1] = a.y; q[4 * v + 2] = a.z; q[4 * v + 3] = a.w;
+                    u[4 * v] = b.x; u[4 * v + 1] = b.y; u[4 * v + 2] = b.z; u[4 * v + 3] = b.w;
+                }
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (!((live >> i) & 1u)) { q[i] = 0.f; u[i] = 0.f; }   // flagged: also kills NaN
+                emit(kb, q, u);
+                emit(kb + 1, q + 16, u + 16);
+                kb += 2;
+            } else {
+                float q[16], u[16];
+                load_kblock(P, src, valid, kb, q, u);
+                emit(kb, q, u);
+                kb += 1;
+            }
         }
     }
     if (P.rscale && valid) {
@@ -694,7 +751,8 @@ cudaError_t launch_split(const rms_plan_s &p, const SplitOpts &o, cudaStream_t s
     sp.vec4 = !chan && (p.nchan % 4 == 0) && !(reinterpret_cast<uintptr_t>(o.Q) & 15) &&
               !(reinterpret_cast<uintptr_t>(o.U) & 15);
     if (sp.mode == MODE_FP16X3 && !o.rexp) return cudaErrorInvalidValue;
-    split_kernel<<<(unsigned)nmt, 128, 0, s>>>(sp);
+    if (!chan && sp.vec4) split_kernel<true><<<(unsigned)nmt, 128, 0, s>>>(sp);
+    else split_kernel<false><<<(unsigned)nmt, 128, 0, s>>>(sp);
     return cudaGetLastError();
 }
 
