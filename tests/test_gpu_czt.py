@@ -175,7 +175,8 @@ def test_czt_rejects_axes_it_cannot_take(rms, inputs):
     assert status(inputs.frequencies(mwa), inputs.phi_grid(mwa)) == rms.RMS_ERR_UNSUPPORTED
 
 
-def test_czt_full_lofar_shape(rms, inputs, oracle_mod):
+@pytest.mark.parametrize("layout", ["chan", "los"])
+def test_czt_full_lofar_shape(rms, inputs, oracle_mod, layout):
     """The full 512^2 x 400 x 401 uniform-lambda^2 cube, generated on the device
     by the seeded generator's twin, in the benchmark's launch configuration;
     sampled rows are regenerated on the host for the oracle."""
@@ -187,8 +188,8 @@ def test_czt_full_lofar_shape(rms, inputs, oracle_mod):
     pidx = torch.empty(cfg.nlos, dtype=torch.int32, device=dev)
     pabs, pphi = torch.empty(cfg.nlos, device=dev), torch.empty(cfg.nlos, device=dev)
     with rms.Plan(freq, phi, PATH, weights=w) as plan:
-        q, u = Lm.generate(plan.handle, cfg, 0, cfg.nlos, "chan")
-        plan.synth(q, u, cfg.nlos, "chan", F, pidx, pabs, pphi)
+        q, u = Lm.generate(plan.handle, cfg, 0, cfg.nlos, layout)
+        plan.synth(q, u, cfg.nlos, layout, F, pidx, pabs, pphi)
         plan.sync()
         rng = np.random.default_rng(99)
         starts = np.r_[0, np.sort(rng.choice(cfg.nlos // 64 - 1, 6, replace=False)) * 64 + 64, cfg.nlos - 64]
