@@ -48,3 +48,20 @@ def test_null_plan_is_rejected(lib):
     out = ctypes.c_void_p(1)
     assert lib.rms_plan_create(ctypes.byref(out), None, 4, 1, None, None, 4, 3, 0) == 1
     assert out.value is None
+
+
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header must compile as C99 and as C++ with no torch or CUDA types
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "rms.h")
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([gcc, "-fsyntax-only", std, "-Wall", "-Werror", "-x", lang, hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    code = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    for t in ("torch", "at::", "cudaStream_t", "cuda_runtime", "float2", "__half", "bfloat16"):
+        assert t not in code, t
