@@ -154,3 +154,33 @@ def test_unit_count_reproduces_the_papers_cost_example():
     cfg = CubeConfig("wsrt_sings_shape", g["nlos"], g["nchan"], 1.3e9, 1.45e9, g["nphi"], -100.0, 100.0, seed=1)
     tflop = cfg.units * g["flop_per_unit"] / 1e12
     assert round(tflop, g["printed_digits"]) == g["tflop_printed"]
+
+
+# ------------------------------------------------------------------- FFT (chirp-z) form of Eq. Fsum
+def test_chirp_z_form_equals_the_direct_sum(oracle_mod):
+    # with lambda^2 uniform (x_j = x_0 + j D) and phi uniform (phi_k = phi_0 + k d), 2 j k =
+    # j^2 + k^2 - (k - j)^2 turns Eq. Fsum into a convolution that FFTs evaluate exactly, for any
+    # d D (no relation to 2 pi / M is needed); the FFT synthesis path relies on this identity
+    rng = np.random.default_rng(21)
+    for nc, nk, l2lo, l2hi, phmax in ((64, 101, 2.8, 6.8, 50.0), (400, 401, 2.84, 6.8, 100.0),
+                                      (120, 333, 1.7, 17.3, 900.0)):
+        lam2 = np.linspace(l2hi, l2lo, nc)
+        w = rng.uniform(0.5, 1.5, nc)
+        w[rng.random(nc) < 0.1] = 0.0
+        phi = np.linspace(-phmax, phmax, nk)
+        Q, U = rng.normal(size=(3, nc)), rng.normal(size=(3, nc))
+        p = oracle_mod.plan(lam2, "lambda2", w)
+        Fo = oracle_mod.synth(Q, U, p, phi)
+        x = lam2 - p.lambda0sq
+        x0, D = x[0], (x[-1] - x[0]) / (nc - 1)
+        p0, d = phi[0], (phi[-1] - phi[0]) / (nk - 1)
+        j, k = np.arange(nc), np.arange(nk)
+        M = int(2 ** np.ceil(np.log2(nc + nk - 1)))
+        a = np.zeros((3, M), complex)
+        a[:, :nc] = w * (Q + 1j * U) * np.exp(-1j * (2 * p0 * D * j + d * D * j * j))
+        m = np.arange(-(nc - 1), nk)
+        h = np.zeros(M, complex)
+        h[m % M] = np.exp(1j * d * D * m * m)
+        c = np.fft.ifft(np.fft.fft(a, axis=1) * np.fft.fft(h), axis=1)[:, :nk]
+        F = p.K * np.exp(-1j * (2 * p0 * x0 + 2 * d * x0 * k + d * D * k * k)) * c
+        assert np.abs(F - Fo).max() <= 1e-10 * np.abs(Fo).max()
