@@ -1,15 +1,18 @@
 #!/usr/bin/env python3
 """Benchmark of RM synthesis on GB300: one JSON line on rank 0.
 
-A step is one rms_synth call over the LOFAR-HBA-like cube (512^2 LOS x 400
-channels, 10% flagged, x 401 phi; FP32 Q/U resident in HBM, complex64 F and
-the peak map written back to HBM) with the plan built once beforehand (the
-phase matrix and RMSF are per-dataset constants, Sec. 2.3).  The metric is
-G(LOS * active channel * phi)/s.
+A step is one rms_synth call over the MWA-like large-phase cube (1024^2 LOS x
+1536 channels 72-231 MHz x 4001 phi in [-2000, 2000] rad/m^2; FP32 Q/U
+resident in HBM, complex64 F (33.6 GB) and the peak map written back to HBM)
+with the plan built once beforehand (the phase matrix and RMSF are
+per-dataset constants, Sec. 2.3).  The metric is G(LOS * active channel * phi)/s.
+The same JSON line carries, as sub-objects, the LOFAR-HBA-like cube
+(512^2 x 400 x 401, `lofar`) and the learned peak proposal on its 2048^2-LOS
+workload (`learned`), each with its own error against the FP64 oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--path bf16x3] [--layout chan]
-  python bench.py --config lofar_lr | lofar_hr [--peak-only]   (the paper's LOFAR cube shapes)
-  python bench.py --config learned   (the learned peak proposal against the full grid)
+  python bench.py --config lofar | precision | lofar_lr | lofar_hr [--peak-only]
+  python bench.py --config learned   (the learned peak proposal against the full grid alone)
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 
 The cube is generated on the device by the seeded generator's device twin; the
@@ -35,13 +38,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RM-synth G(LOS*chan*phi)/s at stated error vs FP64"
 UNIT = "G(LOS*chan*phi)/s"
-CONFIG_NAME = "lofar"
+CONFIG_NAME = "mwa"
+# timed steps per workload when --steps is not given: about 5 s of timed work
+DEFAULT_STEPS = {"mwa": 40, "precision": 60, "lofar_lr": 150, "lofar_hr": 3}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="bf16x3")
@@ -57,7 +62,12 @@ def parse():
     ap.add_argument("--n-train", type=int, default=1 << 20, help="learned workload: training LOS")
     ap.add_argument("--epochs", type=int, default=8, help="learned workload: training epochs")
     ap.add_argument("--hidden", type=int, default=256, help="learned workload: hidden units")
-    return ap.parse_args()
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the LOFAR and learned sub-objects of the default run")
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = DEFAULT_STEPS.get(a.config, 200 if a.config != "learned" else 20)
+    return a
 
 
 def dist_env():
@@ -76,12 +86,13 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="rms_clocks_%d_" % self.dev, suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -102,7 +113,7 @@ class ClockSampler:
         return False
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -120,6 +131,10 @@ class ClockSampler:
                     reasons.add(n)
         # samples under load only: drop the idle head/tail below 50% of max
         load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": statistics.median(load) if load else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -252,99 +267,106 @@ def oracle_sample(cfg, freq, w, phi, L, seconds):
     return {"rows": rows, "Fo": Fo, "peak": oracle.peak(Fo), "plan": op, "baseline": base}
 
 
-def run_ours(args):
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def tensor_roofline(path, useful_flops, kt, timed_s, peaks, traffic, step_ms, hbm_bytes):
+    """Roofline of the contraction kernel (the dominant one): the method's own work,
+    8 flop per (LOS, active channel, phi) unit, over the dense BF16 tensor peak.
+    The split precisions issue three 16-bit products per useful flop, so they can
+    reach at most 1/3 of that peak; the issued products are reported beside it."""
+    terms = 1 if path == "bf16" else 3
+    burst, sust = peaks.get("bf16_tflops"), peaks.get("bf16_tflops_sustained")
+    kind = "measured"
+    if not burst or not sust:
+        burst, sust, kind = 1900.0, 1700.0, "fallback"
+    long_region = timed_s >= 1.0
+    peak = sust if long_region else burst
+    split_ms, gemm_ms, ncalls = kt
+    gemm_launch_ms = gemm_ms / max(1, ncalls)
+    achieved = useful_flops / (gemm_launch_ms * 1e-3) / 1e12
+    return {"kernel": "gemm_kernel (tensor-core contraction + fused epilogue)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "peak_source": "%s %s dense BF16 tensor peak (MEASURED_PEAKS.json %s): the timed region lasted %.2f s, %s"
+                           % (kind, "sustained" if long_region else "burst",
+                              "bf16_tflops_sustained" if long_region else "bf16_tflops", timed_s,
+                              "seconds-long, so the sustained figure applies" if long_region
+                              else "shorter than 1 s, so the burst figure applies"),
+            "frac_of_burst": achieved / burst, "frac_of_sustained": achieved / sust,
+            "issued_products_per_flop": terms, "issued_tflops": achieved * terms,
+            "issued_frac": achieved * terms / peak, "split_ceiling_frac": 1.0 / terms,
+            "launch_ms": gemm_launch_ms, "split_launch_ms": split_ms / max(1, ncalls), "timed_launches": ncalls,
+            "step_frac": useful_flops / (step_ms * 1e-3) / 1e12 / peak,
+            "hbm_gbs_step": hbm_bytes / (step_ms * 1e-3) / 1e9,
+            "algorithmic": "8 flop per (LOS, active channel, phi) unit (one complex multiply-add); achieved = "
+                           "algorithmic flop per launch / the contraction kernel's CUDA-event duration (the "
+                           "library's event hook on the launching stream, averaged over the timed launches); "
+                           "FP16 and BF16 share the dense tensor rate; a split precision issues %d 16-bit products "
+                           "per flop, so split_ceiling_frac is its best possible frac" % terms}
+
+
+def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=1, barrier=None, nlos=None,
+                 peak_only=False, with_paths=False, with_e2e=False, with_cpu=False, with_clean=False,
+                 cpu_seconds=15.0):
+    """Time rms_synth on one workload; return the result fields of a bench line."""
     import dataclasses
     import torch
     import paper_1810_06250_gb300 as rms
     from paper_1810_06250_gb300 import inputs, learned as Lm
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    rms.build()
-    cfg = inputs.CONFIGS[args.config]
-    if args.nlos is not None:
-        cfg = dataclasses.replace(cfg, nlos=args.nlos)
+    from paper_1810_06250_gb300.dist import throughput
+    cfg = inputs.CONFIGS[cfg_name]
+    if nlos is not None:
+        cfg = dataclasses.replace(cfg, nlos=nlos)
     freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
     nact = int(np.count_nonzero(w))
     L = cfg.nlos
-    peak_only = args.peak_only or L * cfg.nphi * 8 > 64e9     # F of the 4000^2 x 7000 cube is 0.9 TB
+    peak_only = peak_only or L * cfg.nphi * 8 > 64e9     # F of the 4000^2 x 7000 cube is 0.9 TB
     stream = torch.cuda.Stream(dev)
     units = L * nact * cfg.nphi
-    barrier = None
-    if world > 1:
-        import torch.distributed as dist
-        barrier = dist.barrier
 
     t_plan0 = time.perf_counter()
-    plan = rms.Plan(freq, phi, args.path, weights=w, device=local)
+    plan = rms.Plan(freq, phi, path, weights=w, device=local)
     plan_ms = 1e3 * (time.perf_counter() - t_plan0)
     # the cube is generated on the device by the seeded generator's device twin
-    q, u = Lm.generate(plan.handle, cfg, 0, L, args.layout)
+    q, u = Lm.generate(plan.handle, cfg, 0, L, layout)
     F = None if peak_only else torch.empty(L, cfg.nphi, 2, device=dev)
     pidx = torch.empty(L, dtype=torch.int32, device=dev)
     pabs = torch.empty(L, device=dev)
     pphi = torch.empty(L, device=dev)
 
     def step():
-        plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
+        plan.synth(q, u, L, layout, F, pidx, pabs, pphi, stream)
 
-    tensor_path = args.path in ("bf16", "bf16x3", "fp16x3")
+    tensor_path = path in ("bf16", "bf16x3", "fp16x3")
     with torch.cuda.stream(stream):
         with ClockSampler(local) as clk:
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 step()
             # the library records events around its two kernels on this stream
             if tensor_path:
                 rms.rms_plan_set_kernel_timing(plan.handle, True)
-            total_ms, per = time_steps(step, stream, args.steps, 0, torch, barrier)
+            total_ms, per = time_steps(step, stream, steps, 0, torch, barrier)
             if tensor_path:
                 rms.rms_plan_set_kernel_timing(plan.handle, False)
     plan.sync(stream)
     kt = rms.rms_plan_kernel_times(plan.handle) if tensor_path else (0.0, 0.0, 0)
-    from paper_1810_06250_gb300.dist import throughput
-    value, tmax = throughput(units, args.steps, total_ms, world, dev)
+    value, tmax = throughput(units, steps, total_ms, world, dev)
     avg_launch_ms = statistics.mean(per)
 
-    # roofline of the dominant kernel (the contraction: one launch per step)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = load_peaks()
     useful_flops = 8.0 * units
-    terms = 1 if args.path == "bf16" else 3
-    hbm_bytes = L * (8.0 * (nact if args.layout == "chan" else cfg.nchan) + (0 if peak_only else 8.0 * cfg.nphi) + 12.0)
+    hbm_bytes = L * (8.0 * (nact if layout == "chan" else cfg.nchan) + (0 if peak_only else 8.0 * cfg.nphi) + 12.0)
+    full_size = nlos is None and not peak_only
     if tensor_path:
-        # the peak for the contraction's own type: a BF16x3 / FP16x3 product costs three
-        # BF16 / FP16 tensor products (FP16 and BF16 run at the same dense rate), so its
-        # peak is the measured BF16 peak / 3; plain BF16 takes the BF16 peak
-        bf16_peak = peaks.get("bf16_tflops_sustained")
-        src = ("measured sustained bf16 (MEASURED_PEAKS.json) / %d" % terms) if bf16_peak else \
-            "fallback 1700 TFLOP/s sustained / %d" % terms
-        bf16_peak = bf16_peak or 1700.0
-        peak = bf16_peak / terms
-        split_ms, gemm_ms, ncalls = kt
-        gemm_launch_ms = gemm_ms / max(1, ncalls)
-        achieved = useful_flops / (gemm_launch_ms * 1e-3) / 1e12
-        traffic = measured_traffic("gemm.cu", "gemm_lofar_bf16x3.md") \
-            if (args.path == "bf16x3" and args.layout == "chan" and args.config == CONFIG_NAME and args.nlos is None
-                and not peak_only) else None
-        roof = {"kernel": "gemm_kernel (tensor-core contraction)", "bound": "tensor", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)", "peak_source": src,
-                "launch_ms": gemm_launch_ms, "split_launch_ms": split_ms / max(1, ncalls),
-                "timed_launches": ncalls,
-                "bf16_peak": bf16_peak, "frac_of_bf16_peak": achieved / bf16_peak,
-                "issued_tflops": achieved * terms, "issued_frac": achieved * terms / bf16_peak,
-                "step_frac": useful_flops / (avg_launch_ms * 1e-3) / 1e12 / peak,
-                "hbm_gbs_step": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9,
-                "algorithmic": "8 flop per (LOS, active channel, phi) (complex MAC); %d tensor products issued "
-                               "per flop; achieved = algorithmic flop per launch / the contraction kernel's "
-                               "CUDA-event duration" % terms}
-    elif args.path == "fp32_czt":
+        traffic = measured_traffic("gemm.cu", "gemm_%s_bf16x3.md" % cfg_name) \
+            if (path == "bf16x3" and layout == "chan" and full_size) else None
+        roof = tensor_roofline(path, useful_flops, kt, total_ms * 1e-3, peaks, traffic, avg_launch_ms, hbm_bytes)
+    elif path == "fp32_czt":
         # FFT synthesis: algorithmic work counted the usual way for FFTs, 5 M log2 M flop per
         # complex length-M transform (two per LOS), 6 flop per complex product (the spectrum
         # times H, and the pre- and post-chirps); bytes are the cube in and F out
@@ -359,7 +381,7 @@ def run_ours(args):
         hbm_peak = peaks.get("hbm_gbs") or 6800.0
         hbm_gbs = hbm_bytes / (avg_launch_ms * 1e-3) / 1e9
         traffic = measured_traffic("czt.cu", "czt_lofar_ul2.md") \
-            if (args.config == "lofar_ul2" and args.layout == "chan" and args.nlos is None and not peak_only) else None
+            if (cfg_name == "lofar_ul2" and layout == "chan" and full_size) else None
         roof = {"kernel": "czt_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
@@ -376,8 +398,7 @@ def run_ours(args):
         peak = props.multi_processor_count * 128 * 2 * clk_mhz * 1e6 / 1e12
         achieved = useful_flops / (avg_launch_ms * 1e-3) / 1e12
         traffic = measured_traffic("simt.cu", "simt_lofar_fp32_table.md") \
-            if (args.path == "fp32_table" and args.layout == "chan" and args.config == CONFIG_NAME
-                and args.nlos is None and not peak_only) else None
+            if (path == "fp32_table" and layout == "chan" and cfg_name == "lofar" and full_size) else None
         roof = {"kernel": "simt_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
@@ -385,21 +406,20 @@ def run_ours(args):
                 "hbm_gbs": hbm_bytes / (avg_launch_ms * 1e-3) / 1e9}
 
     in_gb = L * cfg.nchan * 8 / 1e9
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.path, "data": "synthetic",
-            "config": {"workload": workload_name(cfg, nact, args.layout, peak_only), "nlos_per_gpu": L,
-                       "nchan": cfg.nchan, "nchan_active": nact, "nphi": cfg.nphi, "layout": args.layout,
-                       "l2": "inputs larger than L2 (%.2f GB in%s per step)"
-                             % (in_gb, "" if peak_only else ", %.2f GB out" % (L * cfg.nphi * 8 / 1e9)),
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "units_per_step_total_channels": L * cfg.nchan * cfg.nphi,
-                       "inputs": "device-generated by the seeded generator's device twin; the CPU sample is "
-                                 "regenerated on the host"},
-            "roofline": roof, "gpu_launches": args.steps * (2 if tensor_path else 1),
-            "plan_ms": plan_ms, "clocks": clk.summary()}
+    res = {"value": value, "unit": UNIT, "ms_per_step": tmax / steps, "steps": steps, "warmup": warmup,
+           "dtype": path,
+           "config": {"workload": workload_name(cfg, nact, layout, peak_only), "nlos_per_gpu": L,
+                      "nchan": cfg.nchan, "nchan_active": nact, "nphi": cfg.nphi, "layout": layout,
+                      "l2": "inputs larger than L2 (%.2f GB in%s per step)"
+                            % (in_gb, "" if peak_only else ", %.2f GB out" % (L * cfg.nphi * 8 / 1e9)),
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "units_per_step_total_channels": L * cfg.nchan * cfg.nphi,
+                      "inputs": "device-generated by the seeded generator's device twin; the CPU sample is "
+                                "regenerated on the host"},
+           "roofline": roof, "gpu_launches": steps * (2 if tensor_path else 1), "plan_ms": plan_ms,
+           "clocks": clk.summary()}
 
-    if rank == 0 and world == 1 and not args.no_clean and F is not None and cfg.nphi <= 2048 and tensor_path:
+    if with_clean and F is not None and cfg.nphi <= 2048 and tensor_path:
         # RM-CLEAN of the synthesised cube (FP64 Hogbom iterations, one warp per LOS)
         sigma_f = cfg.sigma * float(np.sqrt(np.sum(w * w)) / np.sum(w))
         thr = 5.0 * sigma_f
@@ -414,16 +434,16 @@ def run_ours(args):
             t_cl, _ = time_steps(clean_step, stream, 3, 1, torch)
         rms.rms_clean_destroy(c)
         mean_it = float(nit.double().mean().item())
-        line["clean"] = {"los_per_call": Lc, "ms_per_call": t_cl / 3, "los_per_s": Lc / (t_cl / 3 * 1e-3),
-                         "gain": 0.1, "max_iter": 1000, "threshold": thr, "threshold_rule": "5 sigma_F",
-                         "mean_iterations": mean_it, "precision": "f64",
-                         "component_updates_per_s": Lc * mean_it * cfg.nphi / (t_cl / 3 * 1e-3)}
+        res["clean"] = {"los_per_call": Lc, "ms_per_call": t_cl / 3, "los_per_s": Lc / (t_cl / 3 * 1e-3),
+                        "gain": 0.1, "max_iter": 1000, "threshold": thr, "threshold_rule": "5 sigma_F",
+                        "mean_iterations": mean_it, "precision": "f64",
+                        "component_updates_per_s": Lc * mean_it * cfg.nphi / (t_cl / 3 * 1e-3)}
         del Fc, nit
 
     # the FP64 oracle on a bounded LOS sample: the CPU baseline, and the error of every path
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(cfg, freq, w, phi, L, args.cpu_seconds)
+    if with_cpu:
+        cpu = oracle_sample(cfg, freq, w, phi, L, cpu_seconds)
         sel = torch.from_numpy(cpu["rows"]).to(dev)
 
     def error_vs_fp64(Fd, pidx_d, pabs_d):
@@ -440,11 +460,11 @@ def run_ours(args):
         return {"peak_abs_rel_max": float(np.max(np.abs(ga - oa) / np.abs(Fo).max(axis=1))),
                 "peak_idx_equal": float(np.mean(pidx_d[sel].cpu().numpy() == oi)), "sample_los": int(len(cpu["rows"]))}
 
-    if rank == 0 and world == 1 and not args.no_paths:
+    if with_paths:
         paths = {}
         for p in ("fp32_fly", "fp32_table", "bf16", "bf16x3", "fp16x3", "fp32_czt"):
-            if p == args.path:
-                paths[p] = {"value": value, "ms_per_step": tmax / args.steps}
+            if p == path:
+                paths[p] = {"value": value, "ms_per_step": tmax / steps}
                 continue
             try:
                 pl = rms.Plan(freq, phi, p, weights=w, device=local)
@@ -454,10 +474,11 @@ def run_ours(args):
                 paths[p] = {"unsupported": "channels not uniform in lambda^2, or nchan + nphi - 1 > 2048"}
                 continue
             with pl:
-                n = 5 if p.startswith("fp32") else 50
+                # about 2 s of timed work per path (the FP32 paths run ~10x longer per step)
+                n = max(3, min(50, int(2000.0 / (tmax / steps) / (8 if p.startswith("fp32") else 1))))
 
                 def st2(pl=pl):
-                    pl.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
+                    pl.synth(q, u, L, layout, F, pidx, pabs, pphi, stream)
                 with torch.cuda.stream(stream):
                     tot, _ = time_steps(st2, stream, n, 2, torch)
                 pl.sync(stream)
@@ -465,49 +486,95 @@ def run_ours(args):
                 if cpu is not None:
                     torch.cuda.synchronize()
                     paths[p]["error_vs_fp64"] = error_vs_fp64(F, pidx, pabs)
-        line["paths"] = paths
+        res["paths"] = paths
         # restore this path's output for the error check below
-        plan.synth(q, u, L, args.layout, F, pidx, pabs, pphi, stream)
+        plan.synth(q, u, L, layout, F, pidx, pabs, pphi, stream)
         plan.sync(stream)
 
-    if rank == 0 and world == 1 and not args.no_e2e and in_gb < 32:
-        Qh = q.cpu().pin_memory()
-        Uh = u.cpu().pin_memory()
-        Fh = None if peak_only else torch.empty(L, cfg.nphi, 2).pin_memory()
-        ih = torch.empty(L, dtype=torch.int32).pin_memory()
-        ah = torch.empty(L).pin_memory()
-        ph = torch.empty(L).pin_memory()
+    if with_e2e and in_gb < 32:
+        Qh = torch.empty(q.shape, dtype=torch.float32, pin_memory=True)
+        Uh = torch.empty(u.shape, dtype=torch.float32, pin_memory=True)
+        Qh.copy_(q)
+        Uh.copy_(u)
+        Fh = None if peak_only else torch.empty(L, cfg.nphi, 2, pin_memory=True)
+        ih = torch.empty(L, dtype=torch.int32, pin_memory=True)
+        ah = torch.empty(L, pin_memory=True)
+        ph = torch.empty(L, pin_memory=True)
 
         def e2e_step():
-            plan.synth_host(Qh, Uh, L, args.layout, Fh, ih, ah, ph, stream)
-        n_e2e = max(3, min(50, args.steps // 20))
+            plan.synth_host(Qh, Uh, L, layout, Fh, ih, ah, ph, stream)
+        n_e2e = max(3, min(50, steps // 20))
         e2e_step()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             e2e_step()
         dt = (time.perf_counter() - t0) / n_e2e
-        line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
-                       "h2d_bytes_per_step": int(Qh.numel() * 4 + Uh.numel() * 4),
-                       "d2h_bytes_per_step": int((0 if Fh is None else Fh.numel() * 4) + L * 12),
-                       "how": "rms_synth_host: pinned host Q/U -> device in LOS chunks, synthesis, F and peak "
-                              "map -> pinned host, copies overlapped on three streams, sync"}
+        res["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
+                      "h2d_bytes_per_step": int(Qh.numel() * 4 + Uh.numel() * 4),
+                      "d2h_bytes_per_step": int((0 if Fh is None else Fh.numel() * 4) + L * 12),
+                      "how": "rms_synth_host: pinned host Q/U -> device in LOS chunks, synthesis, F and peak "
+                             "map -> pinned host, copies overlapped on three streams, sync"}
+        del Qh, Uh, Fh
 
     if cpu is not None:
-        line["cpu_baseline"] = cpu["baseline"]
-        if "clean" in line:
+        res["cpu_baseline"] = cpu["baseline"]
+        if "clean" in res:
             import oracle
             from oracle import clean as oclean
             dphi = float(phi[1] - phi[0])
             R2 = oracle.rmsf(cpu["plan"], (np.arange(2 * len(phi) - 1) - (len(phi) - 1)) * dphi)
             k = min(len(cpu["rows"]), 256)
             t0 = time.perf_counter()
-            oclean.clean(cpu["Fo"][:k], R2, 0.1, 1000, line["clean"]["threshold"], oracle.fwhm_measured(cpu["plan"]),
+            oclean.clean(cpu["Fo"][:k], R2, 0.1, 1000, res["clean"]["threshold"], oracle.fwhm_measured(cpu["plan"]),
                          dphi)
-            line["clean"]["cpu_oracle_los_per_s"] = k / (time.perf_counter() - t0)
-        line["error_vs_fp64"] = error_vs_fp64(F, pidx, pabs)
-        if "paths" in line:
-            line["paths"][args.path]["error_vs_fp64"] = line["error_vs_fp64"]
+            res["clean"]["cpu_oracle_los_per_s"] = k / (time.perf_counter() - t0)
+        res["error_vs_fp64"] = error_vs_fp64(F, pidx, pabs)
+        if "paths" in res:
+            res["paths"][path]["error_vs_fp64"] = res["error_vs_fp64"]
     plan.close()
+    del q, u, F, pidx, pabs, pphi
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_ours(args):
+    import torch
+    import paper_1810_06250_gb300 as rms
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rms.build()
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        barrier = dist.barrier
+    solo = rank == 0 and world == 1
+    res = measure_cube(args, args.config, args.path, args.layout, args.steps, args.warmup, dev, local, world,
+                       barrier, nlos=args.nlos, peak_only=args.peak_only, with_paths=solo and not args.no_paths,
+                       with_e2e=solo and not args.no_e2e, with_cpu=solo and not args.no_cpu,
+                       with_clean=solo and not args.no_clean, cpu_seconds=args.cpu_seconds)
+    line = {"metric": METRIC, "value": res.pop("value"), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.path, "data": "synthetic"}
+    for k in ("steps", "warmup", "unit", "dtype"):
+        res.pop(k, None)
+    line.update(res)
+    if solo and args.config == CONFIG_NAME and args.nlos is None and not args.no_secondary:
+        # the LOFAR-HBA-like cube: a shorter, contraction-lighter workload (23 K blocks of
+        # 16 channels against MWA's 96), BF16x3, channel-major
+        lo = measure_cube(args, "lofar", "bf16x3", "chan", 200, 10, dev, local, with_cpu=not args.no_cpu,
+                          cpu_seconds=5.0)
+        line["lofar"] = {k: lo[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "roofline",
+                                            "clocks", "error_vs_fp64", "cpu_baseline") if k in lo}
+        # the learned peak proposal on its own workload (trained here, on the GPU)
+        try:
+            line["learned"] = measure_learned(args, dev, local, rank, world, None, 10, 3)[0]
+        except Exception as e:   # reported, not hidden: the main line stands on its own
+            line["learned"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -518,24 +585,20 @@ def run_ours(args):
 LEARNED_METRIC = "learned peak map: full-grid-equivalent G(LOS*chan*phi)/s at >=99.5% phi_peak agreement"
 
 
-def run_learned(args):
+def measure_learned(args, dev, local, rank, world, barrier, steps, warmup):
     """The learned proposal on the learned workload (2048^2 LOS, LOFAR band, SNR 5-100).
 
     The network is trained here on the GPU (1M generated LOS labelled by the
     full grid), its confidence threshold calibrated on a separate validation set,
     then one step = one rms_peakmap_learned call over the cube (device-resident
     FP32 Q/U in, peak map out), timed next to the full-grid peak map
-    (rms_synth, peak map only) at the same precision and at plain BF16."""
+    (rms_synth, peak map only) at the same precision and at plain BF16.
+    Returns (the `learned` result object, the fields of a bench line)."""
     import torch
     import paper_1810_06250_gb300 as rms
     from paper_1810_06250_gb300 import inputs, learned as Lm
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    rms.build()
+    path = path if args.config == "learned" else "bf16x3"
+    layout = layout if args.config == "learned" else "chan"
     cfg = inputs.CONFIGS["learned"]
     if args.nlos is not None:
         import dataclasses
@@ -543,15 +606,15 @@ def run_learned(args):
     freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
     nact = int(np.count_nonzero(w))
     L = cfg.nlos
-    plan = rms.Plan(freq, phi, args.path, weights=w, device=local)
+    plan = rms.Plan(freq, phi, path, weights=w, device=local)
     t0 = time.perf_counter()
     net = Lm.Net(plan, hidden=args.hidden, max_batch=4096, seed=101)
     win = Lm.Window(plan, 64)
     hist = Lm.train(plan.handle, net, cfg, n_train=args.n_train, epochs=args.epochs, batch=4096, seed=5001 + rank)
-    tau, cal = Lm.calibrate(plan.handle, net, win, cfg, n_val=1 << 18, seed=6001 + rank, layout=args.layout)
+    tau, cal = Lm.calibrate(plan.handle, net, win, cfg, n_val=1 << 18, seed=6001 + rank, layout=layout)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    Q, U = Lm.generate(plan.handle, cfg, 0, L, args.layout, seed=cfg.seed + 1000 * rank)
+    Q, U = Lm.generate(plan.handle, cfg, 0, L, layout, seed=cfg.seed + 1000 * rank)
     stream = torch.cuda.Stream(dev)
     php = torch.empty(L, device=dev)
     pka = torch.empty(L, device=dev)
@@ -561,65 +624,61 @@ def run_learned(args):
     fphi = torch.empty(L, device=dev)
     fabs = torch.empty(L, device=dev)
     units = L * nact * cfg.nphi
-    barrier = None
-    if world > 1:
-        import torch.distributed as dist
-        barrier = dist.barrier
 
     def learned_step():
-        rms.rms_peakmap_learned(win.handle, net.handle, Q, U, L, args.layout, tau, php, pka, fb, nfb, stream)
+        rms.rms_peakmap_learned(win.handle, net.handle, Q, U, L, layout, tau, php, pka, fb, nfb, stream)
 
     def full_step():
-        plan.synth(Q, U, L, args.layout, None, fidx, fabs, fphi, stream)
+        plan.synth(Q, U, L, layout, None, fidx, fabs, fphi, stream)
 
     with torch.cuda.stream(stream):
         with ClockSampler(local) as clk:
-            t_learn, per = time_steps(learned_step, stream, args.steps, args.warmup, torch, barrier)
-        t_full, _ = time_steps(full_step, stream, max(3, args.steps // 2), 2, torch)
+            t_learn, per = time_steps(learned_step, stream, steps, warmup, torch, barrier)
+        t_full, _ = time_steps(full_step, stream, max(3, steps // 2), 2, torch)
         with rms.Plan(freq, phi, "bf16", weights=w, device=local) as p1:
             def bf16_step():
-                p1.synth(Q, U, L, args.layout, None, fidx, fabs, fphi, stream)
-            t_bf16, _ = time_steps(bf16_step, stream, max(3, args.steps // 2), 2, torch)
+                p1.synth(Q, U, L, layout, None, fidx, fabs, fphi, stream)
+            t_bf16, _ = time_steps(bf16_step, stream, max(3, steps // 2), 2, torch)
         # the full grid at the window's resolution (step D/2 over the same range: the
         # fine grid every window is cut from), same precision
         phi_fine = cfg.phi_min + 0.5 * (phi[1] - phi[0]) * np.arange(2 * cfg.nphi - 1)
         gidx = torch.empty(L, dtype=torch.int32, device=dev)
         gphi = torch.empty(L, device=dev)
         gabs = torch.empty(L, device=dev)
-        with rms.Plan(freq, phi_fine, args.path, weights=w, device=local) as p2:
+        with rms.Plan(freq, phi_fine, path, weights=w, device=local) as p2:
             def fine_step():
-                p2.synth(Q, U, L, args.layout, None, gidx, gabs, gphi, stream)
-            t_fine, _ = time_steps(fine_step, stream, max(3, args.steps // 2), 2, torch)
+                p2.synth(Q, U, L, layout, None, gidx, gabs, gphi, stream)
+            t_fine, _ = time_steps(fine_step, stream, max(3, steps // 2), 2, torch)
             fine_step()
         full_step()
         learned_step()
     torch.cuda.synchronize()
     plan.sync(stream)
-    ms_learn = t_learn / args.steps
-    ms_full = t_full / max(3, args.steps // 2)
-    ms_bf16 = t_bf16 / max(3, args.steps // 2)
-    ms_fine = t_fine / max(3, args.steps // 2)
+    ms_learn = t_learn / steps
+    ms_full = t_full / max(3, steps // 2)
+    ms_bf16 = t_bf16 / max(3, steps // 2)
+    ms_fine = t_fine / max(3, steps // 2)
     agree = float(np.mean(np.abs(php.cpu().numpy().astype(np.float64) - fphi.cpu().numpy()) <= 0.5 * (1 + 1e-6)))
     dfine = np.abs(php.cpu().numpy().astype(np.float64) - gphi.cpu().numpy())
     agree_fine_point = float(np.mean(dfine <= 1e-3))
     agree_fine = float(np.mean(dfine <= 0.5 * (1 + 1e-6)))
     fbr = float(fb.cpu().numpy().mean())
     from paper_1810_06250_gb300.dist import throughput
-    value, tmax = throughput(units, args.steps, t_learn, world, dev)
+    value, tmax = throughput(units, steps, t_learn, world, dev)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6701.0)
-    in_bytes = L * 8.0 * (nact if args.layout == "chan" else cfg.nchan)
+    in_bytes = L * 8.0 * (nact if layout == "chan" else cfg.nchan)
     alg = in_bytes + 8.0 * L
-    line = {"metric": LEARNED_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.path, "data": "synthetic",
+    line = {"metric": LEARNED_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": tmax / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": path, "data": "synthetic",
             "config": {"workload": "learned: 2048x2048 LOS x 400 channels (%d active) 115-178 MHz x 401 phi in "
                                    "[-100, 100], FP32 Q/U %s-major, peak map only; 1-3 thin/Burn-slab components, "
-                                   "SNR 5-100; window 64 x 0.25 rad/m^2" % (nact, args.layout),
+                                   "SNR 5-100; window 64 x 0.25 rad/m^2" % (nact, layout),
                        "nlos_per_gpu": L, "l2": "inputs larger than L2 (13.4 GB per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "learned": {"speedup_vs_full_grid_same_precision": ms_full / ms_learn,
@@ -636,14 +695,15 @@ def run_learned(args):
                          "unit": "GB/s", "frac": alg / (ms_learn * 1e-3) / 1e9 / hbm_peak, "traffic": None,
                          "algorithmic": "cube read once (8 B per LOS x contraction channel) + 8 B peak map per LOS",
                          "peak_source": "measured HBM copy (MEASURED_PEAKS.json)"},
-            "gpu_launches": args.steps * 9, "clocks": clk.summary()}
-    if rank == 0 and world == 1 and not args.no_e2e:
-        Qh = torch.empty(Q.shape, dtype=torch.float32).pin_memory()
-        Uh = torch.empty(U.shape, dtype=torch.float32).pin_memory()
+            "gpu_launches": steps * 9, "clocks": clk.summary()}
+    solo = rank == 0 and world == 1 and args.config == "learned"
+    if solo and not args.no_e2e:
+        Qh = torch.empty(Q.shape, dtype=torch.float32, pin_memory=True)
+        Uh = torch.empty(U.shape, dtype=torch.float32, pin_memory=True)
         Qh.copy_(Q)
         Uh.copy_(U)
-        ph_h = torch.empty(L).pin_memory()
-        pa_h = torch.empty(L).pin_memory()
+        ph_h = torch.empty(L, pin_memory=True)
+        pa_h = torch.empty(L, pin_memory=True)
 
         def e2e():
             with torch.cuda.stream(stream):
@@ -662,7 +722,7 @@ def run_learned(args):
         line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
                        "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(L * 8),
                        "how": "pinned host Q/U -> device, rms_peakmap_learned, phi_peak and |F|_peak -> pinned host"}
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if solo and not args.no_cpu:
         import oracle
         oracle.build()
         op = oracle.plan(freq, "freq", w)
@@ -681,6 +741,30 @@ def run_learned(args):
     net.close()
     win.close()
     plan.close()
+    del Q, U
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    learned = line.pop("learned")
+    learned.update({"ms_per_step": line["ms_per_step"], "value_full_grid_equivalent": line["value"],
+                    "unit": UNIT, "dtype": path, "workload": line["config"]["workload"],
+                    "roofline": line["roofline"], "clocks": line["clocks"]})
+    return learned, line
+
+
+def run_learned(args):
+    import torch
+    import paper_1810_06250_gb300 as rms
+    rank, world, local = dist_env()
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = dist.barrier
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rms.build()
+    learned, line = measure_learned(args, dev, local, rank, world, barrier, args.steps, args.warmup)
+    line["learned"] = learned
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -225,17 +225,20 @@ rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64
  * framework whose own allocator owns the device's memory budget.  rms_synth on
  * an FP16X3 plan takes a one-byte-per-LOS scratch from the stream-ordered pool
  * for every call; here that scratch is a fixed device array of
- * RMS_NOALLOC_MAX_LOS bytes compiled into the library, which every GPU that
- * loads the library holds until the process exits.
+ * RMS_NOALLOC_MAX_LOS bytes compiled into the library.  It becomes resident on a
+ * device, together with the code of the kernels this call launches, when the
+ * first FP16X3 plan is created there (rms_plan_create looks up the array's
+ * address with cudaGetSymbolAddress and loads the kernels, so that lazy module
+ * loading cannot allocate during a call), and it stays until the process exits.
  *
- * Same arguments and results as rms_synth.  Returns RMS_ERR_INVALID_ARG when
+ * Same arguments and checks as rms_synth.  Returns RMS_ERR_INVALID_ARG when
  * nlos > RMS_NOALLOC_MAX_LOS (nothing is launched) and RMS_ERR_UNSUPPORTED for a
  * plan of another precision (rms_synth allocates nothing for those already).
- * Calls no cudaMalloc, cudaFree or pool allocation.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls in the process share the one
- * array and every call rewrites the entries it uses, so calls whose kernels
- * overlap on the GPU race: do not run two at once, on any plans or streams.
+ * Calls no cudaMalloc, cudaFree or pool allocation.  All calls in the process
+ * share the one array and every call rewrites the entries it uses, so calls
+ * whose kernels overlap on the GPU race: do not run two at once, on any plans
+ * or streams.  The kernel-timing hook (rms_plan_set_kernel_timing) records
+ * nothing for these calls.
  */
 #define RMS_NOALLOC_MAX_LOS (1 << 22)
 rms_status rms_synth_noalloc(rms_plan_t plan, const float *Q, const float *U, int64_t nlos, int32_t layout,
@@ -472,6 +475,15 @@ rms_status rms_train_step(rms_net_t net, const float *Q, const float *U, int64_t
  */
 rms_status rms_window_create(rms_window_t *win, rms_plan_t plan, int32_t width);
 rms_status rms_window_destroy(rms_window_t win);
+
+/*
+ * The window centre rms_peakmap_learned uses for each proposal: fine point
+ * 2 bin[l], clamped into width/2 .. 2 (nphi - 1) - width/2 + 1 so that the whole
+ * window lies on the fine grid.  bin, centre: device [nlos] int32.
+ * Asynchronous on stream; allocates nothing.  RMS_ERR_INVALID_ARG for a NULL
+ * window or array, or nlos < 0.
+ */
+rms_status rms_window_centres(rms_window_t win, const int32_t *bin, int64_t nlos, int32_t *centre, void *stream);
 
 /*
  * Exact synthesis on one window per LOS.  centre: device [nlos] int32, the

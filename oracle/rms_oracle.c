@@ -13,7 +13,7 @@
  * over all Faraday depths (Sec. 3, the Brentjens CPU strategy).  cos/sin are
  * called on the full, unreduced double argument; glibc reduces it exactly.
  *
- * Readings of the paper taken here (each listed in the design doc):
+ * Readings of the paper taken here:
  *  - lambda_0^2 is the weighted mean of lambda_i^2 over the weights
  *    (Sec. 2.2 says "mean of lambda_i^2"; weighted = plain mean for uniform
  *    weights and makes dR/dphi(0) = 0).

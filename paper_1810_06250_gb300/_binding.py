@@ -36,7 +36,7 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
            "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout", "rms_clean_create",
-           "rms_clean_destroy", "rms_clean", "rms_refine_peaks")
+           "rms_clean_destroy", "rms_clean", "rms_refine_peaks", "rms_window_centres")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
             "rms_window_create": [ctypes.POINTER(P), P, _i32],
             "rms_window_destroy": [P],
             "rms_synth_window": [P, P, P, _i64, _i32, P, P, P, P, P, P],
+            "rms_window_centres": [P, P, _i64, P, P],
             "rms_peakmap_learned": [P, P, P, P, _i64, _i32, ctypes.c_float, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -341,6 +342,13 @@ def rms_window_create(plan: int, width: int) -> int:
 
 def rms_window_destroy(win: int):
     _check(load().rms_window_destroy(win), "rms_window_destroy")
+
+
+def rms_window_centres(win: int, bin_, nlos: int, centre, stream=None):
+    import torch
+    st = load().rms_window_centres(win, _dptr(bin_, torch.int32, "bin"), int(nlos), _dptr(centre, torch.int32, "centre"),
+                                   _stream(stream))
+    _check(st, "rms_window_centres")
 
 
 def rms_synth_window(win: int, Q, U, nlos: int, layout, centre, F_out=None, widx=None, wabs=None, wphi=None,

@@ -347,6 +347,8 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
         }
     }
     RMS_TRY(cudaEventCreateWithFlags(&p->last, cudaEventDisableTiming));
+    // rms_synth_noalloc on this plan must find its array and kernels loaded on the device
+    if (precision == RMS_FP16X3) RMS_TRY(noalloc_prepare(device));
     if (is_tensor(precision)) {
         // rms_synth takes per-call scratch from the device's default stream-ordered
         // pool; keep freed blocks reserved there so calls do not go back to the driver
@@ -481,8 +483,9 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
     return from_cuda(e);
 }
 
-static rms_status check_synth_args(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
-                                   float *F)
+extern "C++" {
+rms_status check_synth_args(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
+                            float *F)
 {
     if (!p || !Q || !U || nlos < 0) return RMS_ERR_INVALID_ARG;
     if (layout != RMS_CHAN_MAJOR && layout != RMS_LOS_MAJOR) return RMS_ERR_INVALID_ARG;
@@ -491,6 +494,7 @@ static rms_status check_synth_args(rms_plan_t p, const float *Q, const float *U,
     if (nlos > ((int64_t)1 << 40) / ((int64_t)p->nchan + p->nphi)) return RMS_ERR_INVALID_ARG;
     return RMS_OK;
 }
+}  // extern "C++"
 
 rms_status rms_synth(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout, float *F_out,
                      int32_t *peak_idx, float *peak_abs, float *phi_peak, void *stream)

@@ -204,6 +204,17 @@ rms_status rms_window_destroy(rms_window_t w)
     return RMS_OK;
 }
 
+rms_status rms_window_centres(rms_window_t w, const int32_t *bin, int64_t nlos, int32_t *centre, void *stream)
+{
+    if (!w || !bin || !centre || nlos < 0 || nlos > ((int64_t)1 << 31) - 128) return RMS_ERR_INVALID_ARG;
+    if (nlos == 0) return RMS_OK;
+    Guard guard(w->device);
+    if (!guard.ok) return RMS_ERR_CUDA;
+    centre_kernel<<<(unsigned)((nlos + 255) / 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        bin, nlos, w->cmin, w->cmax, centre);
+    return from_cuda(cudaGetLastError());
+}
+
 rms_status rms_synth_window(rms_window_t w, const float *Q, const float *U, int64_t nlos, int32_t layout,
                             const int32_t *centre, float *F_out, int32_t *widx, float *wabs, float *wphi,
                             void *stream)

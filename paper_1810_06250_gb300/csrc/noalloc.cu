@@ -19,6 +19,7 @@ std::mutex g_mu;
 int8_t *g_rexp_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_rexp on the current device (looked up once per device).
+// The lookup loads this file's module on the device, and with it the array.
 cudaError_t rexp_address(int device, int8_t **out)
 {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
@@ -35,14 +36,25 @@ cudaError_t rexp_address(int device, int8_t **out)
 
 }  // namespace
 
+// Called by rms_plan_create for FP16X3 plans, with the plan's device current:
+// everything rms_synth_noalloc needs on a device is loaded here, where allocating
+// is allowed -- the array (through its address lookup) and the code of the two
+// kernels it launches -- so that with lazy module loading no later call makes the
+// driver allocate module memory.
+cudaError_t noalloc_prepare(int device)
+{
+    int8_t *p = nullptr;
+    cudaError_t e = rexp_address(device, &p);
+    if (e == cudaSuccess) e = umma_prepare();
+    return e;
+}
+
 extern "C" rms_status rms_synth_noalloc(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout,
                                         float *F_out, int32_t *peak_idx, float *peak_abs, float *phi_peak,
                                         void *stream)
 {
-    if (!p || !Q || !U || nlos < 0) return RMS_ERR_INVALID_ARG;
-    if (layout != RMS_CHAN_MAJOR && layout != RMS_LOS_MAJOR) return RMS_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(Q) & 3) || (reinterpret_cast<uintptr_t>(U) & 3)) return RMS_ERR_INVALID_ARG;
-    if (F_out && (reinterpret_cast<uintptr_t>(F_out) & 7)) return RMS_ERR_INVALID_ARG;
+    const rms_status st = check_synth_args(p, Q, U, nlos, layout, F_out);   // the checks of rms_synth
+    if (st != RMS_OK) return st;
     if (nlos > RMS_NOALLOC_MAX_LOS) return RMS_ERR_INVALID_ARG;   // beyond the fixed scratch
     if (p->precision != RMS_FP16X3) return RMS_ERR_UNSUPPORTED;
     if (*p->h_err) return RMS_ERR_TIMEOUT;

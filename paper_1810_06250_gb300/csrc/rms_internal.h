@@ -106,6 +106,14 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
                         const int8_t *rexp, cudaStream_t s);
 cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos,
                                 int layout, int8_t *rexp, cudaStream_t s);
+// loads umma.cu's kernels on the current device (cudaFuncGetAttributes) and checks the register split
+cudaError_t umma_prepare();
+
+// noalloc.cu: loads what rms_synth_noalloc needs on the current device (plan creation, FP16X3)
+cudaError_t noalloc_prepare(int device);
+
+// api.cu: argument checks shared by the synthesis entry points
+rms_status check_synth_args(rms_plan_t p, const float *Q, const float *U, int64_t nlos, int32_t layout, float *F);
 
 // gemm.cu: split kernel (layout stage) + contraction kernel
 // Split operand image: [ceil(rows / 128)][kblocks][16 KB], K blocks of 16 channels

@@ -750,20 +750,25 @@ cudaError_t launch_row_exponent(const rms_plan_s &p, const float *Q, const float
     return cudaGetLastError();
 }
 
+cudaError_t umma_prepare()
+{
+    // setmaxnreg moves registers between warpgroups inside the block's launch
+    // allotment (512 threads x registers per thread); the split used here adds up
+    // to exactly 512 x 128, so refuse any build whose kernel was not given 128.
+    // cudaFuncGetAttributes also loads this file's module on the current device.
+    cudaFuncAttributes fa, fr;
+    cudaError_t e = cudaFuncGetAttributes(&fa, umma_synth_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fr, row_exponent_kernel);
+    if (e != cudaSuccess) return e;
+    return (fa.numRegs == 128 && 256 * (kRegsLow + kRegsHigh) == kThreads * 128) ? cudaSuccess
+                                                                                : cudaErrorInvalidConfiguration;
+}
+
 cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout, float *F,
                         int32_t *pidx, float *pabs, float *pphi, const int8_t *rexp, cudaStream_t s)
 {
-    static int checked = 0;   // 1: register split verified, -1: refused
-    if (checked == 0) {
-        // setmaxnreg moves registers between warpgroups inside the block's launch
-        // allotment (512 threads x registers per thread); the split used here adds up
-        // to exactly 512 x 128, so refuse any build whose kernel was not given 128.
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, umma_synth_kernel);
-        if (e != cudaSuccess) return e;
-        checked = (fa.numRegs == 128 && 256 * (kRegsLow + kRegsHigh) == kThreads * 128) ? 1 : -1;
-    }
-    if (checked < 0) return cudaErrorInvalidConfiguration;
+    const cudaError_t reg_check = umma_prepare();
+    if (reg_check != cudaSuccess) return reg_check;
 
     const bool chan = layout == RMS_CHAN_MAJOR;
     UmmaParams P;
@@ -797,13 +802,9 @@ cudaError_t launch_umma(const rms_plan_s &p, const float *Q, const float *U, int
     CUtensorMap tq, tu;
     std::memset(&tq, 0, sizeof(tq));
     std::memset(&tu, 0, sizeof(tu));
-    // RMS_DATA_TMA=0 in the environment forces the converters' direct global loads
-    static const int tma_allowed = [] {
-        const char *v = std::getenv("RMS_DATA_TMA");
-        return (v && v[0] == '0') ? 0 : 1;
-    }();
-    P.use_tma = tma_allowed && encode_data_map(&tq, Q, nlos, p.nchan, layout) &&
-                encode_data_map(&tu, U, nlos, p.nchan, layout);
+    // TMA staging of the FP32 data needs 16-byte aligned bases and rows; otherwise
+    // the converters load it directly from global memory
+    P.use_tma = encode_data_map(&tq, Q, nlos, p.nchan, layout) && encode_data_map(&tu, U, nlos, p.nchan, layout);
     P.sd = P.use_tma ? 3 : 0;
     P.sa = 3;
     P.sb = umma_bstages(p.tile_n, P.sd, P.sa);

@@ -161,8 +161,8 @@ def calibrate(plan: int, net: Net, win: Window, cfg: CubeConfig, n_val: int, tar
     bin_ = torch.empty(n_val, dtype=torch.int32, device="cuda")
     conf = torch.empty(n_val, dtype=torch.float32, device="cuda")
     B.rms_propose(net.handle, Q, U, n_val, layout, win.conf_halfwidth, None, bin_, conf)
-    lo, hi = win.width // 2, 2 * (cfg.nphi - 1) - win.width // 2 + 1
-    centre = torch.from_numpy(np.clip(2 * bin_.cpu().numpy(), lo, hi).astype(np.int32)).cuda()
+    centre = torch.empty(n_val, dtype=torch.int32, device="cuda")
+    B.rms_window_centres(win.handle, bin_, n_val, centre)      # the centres rms_peakmap_learned uses
     widx = torch.empty(n_val, dtype=torch.int32, device="cuda")
     wphi = torch.empty(n_val, dtype=torch.float32, device="cuda")
     B.rms_synth_window(win.handle, Q, U, n_val, layout, centre, None, widx, None, wphi)

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-# Per-LOS error gates e = max_k |F_gpu - F_orc| / max_k |F_orc| (see DESIGN.md):
+# Per-LOS error gates e = max_k |F_gpu - F_orc| / max_k |F_orc|:
 #   split-precision tensor paths, the FP32 table path and FP32 chirp-z FFTs: 1e-5 (the stated target);
 #   plain BF16: 1e-3 relative to the cube's max |F| (its per-LOS tail is ~3e-3);
 #   FP32 on-the-fly sincos (the paper's own method): reported, sanity gate only.

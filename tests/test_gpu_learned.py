@@ -180,7 +180,7 @@ def test_gradients_match_oracle(rms, inputs, L, layout):
         for k in ("W1", "b1", "W2", "b2"):
             c = cosine(g[k].astype(np.float64), gq[k])
             rel = np.linalg.norm(g[k] - gq[k]) / np.linalg.norm(gq[k])
-            assert c >= 0.999 and rel <= 0.03, (k, c, rel)
+            assert c >= 0.999 and rel <= 2e-2, (k, c, rel)
             # and close to the unquantised network's gradient (ReLU masks of
             # near-zero pre-activations may differ there)
             assert cosine(g[k].astype(np.float64), gr[k]) >= 0.99, k
@@ -258,6 +258,21 @@ def test_window_synthesis_matches_oracle(rms, inputs, L, oracle_mod, layout, pre
         # (plain BF16's tolerance is relative to the cube: few weak windows clear it)
         assert clear.mean() > (0.9 if precision == "bf16x3" else 0.1)
         np.testing.assert_array_equal(kg[clear], np.argmax(a, axis=1)[clear])
+
+
+def test_window_centres_match_oracle(rms, inputs, L):
+    """rms_window_centres (the centres the learned peak map uses; calibration takes
+    them from here) equals the oracle's window_centre, including both clamps."""
+    cfg, plan = lofar_plan(rms, inputs)
+    with plan:
+        for W in (8, 64, 128):
+            win = L.Window(plan, W)
+            bins = np.concatenate([np.arange(cfg.nphi), [0, 1, 3, cfg.nphi - 1, cfg.nphi - 2]]).astype(np.int32)
+            c = torch.full((len(bins),), -5, dtype=torch.int32, device="cuda")
+            rms.rms_window_centres(win.handle, dev(bins), len(bins), c)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(c.cpu().numpy(), onet.window_centre(bins, cfg.nphi, W))
+            win.close()
 
 
 def test_window_thin_source_on_fine_grid(rms, inputs, L):

@@ -239,9 +239,9 @@ def test_lofar_full(rms, inputs, oracle_mod, lofar, path, layout):
 
 
 # ------------------------------------------------------------------- large cubes
-LARGE = [("precision", "bf16x3", 2048), ("precision", "bf16", 512), ("precision", "fp32_fly", 512),
-         ("precision", "fp32_table", 512), ("mwa", "bf16x3", 256), ("mwa", "fp16x3", 256),
-         ("lofar_lr", "bf16x3", 256)]
+LARGE = [("precision", "bf16x3", 2048), ("precision", "bf16", 512), ("precision", "fp16x3", 512),
+         ("precision", "fp32_fly", 512), ("precision", "fp32_table", 512), ("mwa", "bf16x3", 256),
+         ("mwa", "fp16x3", 256), ("mwa", "bf16", 256), ("lofar_lr", "bf16x3", 256)]
 
 
 @pytest.mark.parametrize("cfg_name,path,nsample", LARGE)

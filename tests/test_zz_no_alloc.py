@@ -2,11 +2,14 @@
 
 It exists for callers that cannot allocate device memory while they process
 data (memory reserved up front, or owned by another allocator).  Its results
-must match rms_synth's on the same plan, call after call, although every call
-reuses the same fixed scratch array (within the FP16X3 tolerance: the two
-kernels fold their partial sums in different groups).  This file is collected
-last on purpose.
+must match rms_synth's on the same plan and the FP64 oracle, call after call,
+although every call reuses the same fixed scratch array (within the FP16X3
+tolerance: the two kernels fold their partial sums in different groups), and a
+run of calls must leave the device's memory exactly as it found it.  This file
+is collected last on purpose.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -34,7 +37,7 @@ def _outputs(nlos, nphi):
 
 
 @pytest.mark.parametrize("layout", ["chan", "los"])
-def test_noalloc_matches_rms_synth(rms, layout):
+def test_noalloc_matches_rms_synth(rms, oracle_mod, layout):
     from paper_1810_06250_gb300 import inputs
     cfg = inputs.CONFIGS["lofar"]
     freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
@@ -63,6 +66,13 @@ def test_noalloc_matches_rms_synth(rms, layout):
                 gh.check_peaks_self(F, i.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy(), phi)
             gh.check_peaks_oracle(i1.cpu().numpy(), Fa[..., 0] + 1j * Fa[..., 1], gh.TOL["fp16x3"])
             np.testing.assert_allclose(a1.cpu().numpy(), a0.cpu().numpy(), rtol=2 * gh.TOL["fp16x3"])
+            # and against the FP64 oracle on a sample of rows spread over the call
+            rows = np.arange(0, nlos, 79)
+            op = oracle_mod.plan(freq, "freq", w)
+            Fo = oracle_mod.synth(Q[rows], U[rows], op, phi)
+            ok, info = gh.gate("fp16x3", Fb[rows], Fo)
+            assert ok, info
+            gh.check_peaks_oracle(i1.cpu().numpy()[rows], Fo, gh.TOL["fp16x3"])
 
 
 def test_noalloc_limits(rms):
@@ -78,3 +88,49 @@ def test_noalloc_limits(rms):
         with pytest.raises(rms.RmsError) as e:
             rms.rms_synth_noalloc(plan.handle, q, q, 8, "chan", None, q.view(torch.int32))
         assert e.value.status == rms.RMS_ERR_UNSUPPORTED
+
+
+def _device_memory_state(index):
+    """(default pool: reserved now, reserved high-water mark, used now, used
+    high-water mark; free device bytes) through the CUDA driver API."""
+    cu = ctypes.CDLL("libcuda.so.1")
+    dev = ctypes.c_int()
+    assert cu.cuDeviceGet(ctypes.byref(dev), index) == 0
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
+    vals = []
+    for attr in (5, 6, 7, 8):   # CU_MEMPOOL_ATTR_{RESERVED,USED}_MEM_{CURRENT,HIGH} (cuda.h order)
+        v = ctypes.c_uint64()
+        assert cu.cuMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+        vals.append(v.value)
+    free, total = ctypes.c_size_t(), ctypes.c_size_t()
+    assert cu.cuMemGetInfo_v2(ctypes.byref(free), ctypes.byref(total)) == 0
+    return vals + [free.value], cu, pool
+
+
+def test_noalloc_allocates_nothing(rms):
+    """After the plan exists (which loads the array and the kernels), a run of calls
+    changes neither the pool's reserved or used bytes -- not even for a moment:
+    the high-water marks are reset first -- nor the device's free memory."""
+    from paper_1810_06250_gb300 import inputs
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = inputs.frequencies(cfg), inputs.weights(cfg), inputs.phi_grid(cfg)
+    nlos = 8192
+    dev = torch.device("cuda")
+    Q, U = inputs.make_cube(cfg, 0, nlos)
+    q = torch.from_numpy(inputs.to_layout(Q, "chan")).to(dev)
+    u = torch.from_numpy(inputs.to_layout(U, "chan")).to(dev)
+    F, i, a, p = _outputs(nlos, cfg.nphi)
+    with rms.Plan(freq, phi, "fp16x3", weights=w) as plan:
+        torch.cuda.synchronize()
+        before, cu, pool = _device_memory_state(torch.cuda.current_device())
+        for attr in (6, 8):         # reset the high-water marks to the current values
+            zero = ctypes.c_uint64(0)
+            assert cu.cuMemPoolSetAttribute(pool, attr, ctypes.byref(zero)) == 0
+        before, _, _ = _device_memory_state(torch.cuda.current_device())
+        for _ in range(4):
+            rms.rms_synth_noalloc(plan.handle, q, u, nlos, "chan", F, i, a, p)
+        plan.sync()
+        torch.cuda.synchronize()
+        after, _, _ = _device_memory_state(torch.cuda.current_device())
+    assert after == before, (before, after)
