@@ -70,7 +70,7 @@ def test_noalloc_matches_rms_synth(rms, oracle_mod, layout):
             rows = np.arange(0, nlos, 79)
             op = oracle_mod.plan(freq, "freq", w)
             Fo = oracle_mod.synth(Q[rows], U[rows], op, phi)
-            ok, info = gh.gate("fp16x3", Fb[rows], Fo)
+            ok, info = gh.gate("fp16x3", Fb[rows][..., 0] + 1j * Fb[rows][..., 1], Fo)
             assert ok, info
             gh.check_peaks_oracle(i1.cpu().numpy()[rows], Fo, gh.TOL["fp16x3"])
 
