@@ -355,6 +355,10 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
                 rms.rms_plan_set_kernel_timing(plan.handle, False)
     plan.sync(stream)
     kt = rms.rms_plan_kernel_times(plan.handle) if tensor_path else (0.0, 0.0, 0)
+    sched = {k: rms.rms_plan_info(plan.handle, v) for k, v in
+             (("ctas", rms.RMS_INFO_LAST_CTAS), ("cta_pairs", rms.RMS_INFO_LAST_PAIR),
+              ("n_panels", rms.RMS_INFO_LAST_PANELS), ("kernels_per_step", rms.RMS_INFO_LAST_KERNELS))} \
+        if tensor_path else None
     value, tmax = throughput(units, steps, total_ms, world, dev)
     avg_launch_ms = statistics.mean(per)
 
@@ -366,6 +370,9 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
         traffic = measured_traffic("gemm.cu", "gemm_%s_bf16x3.md" % cfg_name) \
             if (path == "bf16x3" and layout == "chan" and full_size) else None
         roof = tensor_roofline(path, useful_flops, kt, total_ms * 1e-3, peaks, traffic, avg_launch_ms, hbm_bytes)
+        roof["schedule"] = dict(sched, note="n_panels 0: each CTA runs every phase tile of its M tile; k > 0: "
+                                            "single-tile jobs in k panels of the phase matrix, peaks merged by "
+                                            "64-bit atomics and a finalize kernel")
     elif path == "fp32_czt":
         # FFT synthesis: algorithmic work counted the usual way for FFTs, 5 M log2 M flop per
         # complex length-M transform (two per LOS), 6 flop per complex product (the spectrum
@@ -416,7 +423,7 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
                       "units_per_step_total_channels": L * cfg.nchan * cfg.nphi,
                       "inputs": "device-generated by the seeded generator's device twin; the CPU sample is "
                                 "regenerated on the host"},
-           "roofline": roof, "gpu_launches": steps * (2 if tensor_path else 1), "plan_ms": plan_ms,
+           "roofline": roof, "gpu_launches": steps * (sched["kernels_per_step"] if sched else 1), "plan_ms": plan_ms,
            "clocks": clk.summary()}
 
     if with_clean and F is not None and cfg.nphi <= 2048 and tensor_path:

@@ -255,7 +255,13 @@ enum {
     RMS_INFO_KPAD = 4,        /* padded contraction length of the tensor-core operand */
     RMS_INFO_NPAD = 5,        /* padded rows (2 * nphi rounded up) of the phase matrix */
     RMS_INFO_TILE_N = 6,      /* phase-matrix rows per tensor-core tile */
-    RMS_INFO_DEVICE = 7
+    RMS_INFO_DEVICE = 7,
+    /* what the last tensor-core rms_synth / rms_synth_peaks / rms_synth_host call ran: */
+    RMS_INFO_LAST_CTAS = 8,   /* persistent CTAs of the contraction kernel */
+    RMS_INFO_LAST_PAIR = 9,   /* 1: CTA pairs (two SMs per 256-row MMA), 0: single CTAs */
+    RMS_INFO_LAST_PANELS = 10, /* 0: each CTA ran all phase tiles of its lines of sight;
+                                  k > 0: single-tile jobs in k panels of the phase matrix */
+    RMS_INFO_LAST_KERNELS = 11 /* kernels the call launched */
 };
 rms_status rms_plan_info(rms_plan_t plan, int32_t what, int64_t *value);
 

@@ -15,7 +15,8 @@ from ._binding import (  # noqa: F401
     RMS_FP32_SIMT_FLY, RMS_FP32_SIMT_TABLE, RMS_GET_ACTIVE, RMS_GET_B_HI, RMS_GET_B_LO,
     RMS_GET_LAMBDA2, RMS_GET_RMSF64, RMS_GET_TABLE, RMS_INFO_DEVICE, RMS_INFO_KPAD,
     RMS_INFO_NCHAN, RMS_INFO_NCHAN_ACTIVE, RMS_INFO_NPAD, RMS_INFO_NPHI, RMS_INFO_PRECISION,
-    RMS_INFO_TILE_N, RMS_LOS_MAJOR, RMS_OK,
+    RMS_INFO_TILE_N, RMS_INFO_LAST_CTAS, RMS_INFO_LAST_PAIR, RMS_INFO_LAST_PANELS, RMS_INFO_LAST_KERNELS,
+    RMS_LOS_MAJOR, RMS_OK,
     RMS_NOALLOC_MAX_LOS, load, rms_plan_create, rms_plan_destroy, rms_plan_get, rms_plan_info, rms_plan_set_timeout,
     rms_plan_sync, rms_rmsf, rms_status_string, rms_synth, rms_synth_host, rms_synth_noalloc,
     RMS_NET_GRADS, RMS_NET_HIDDEN, RMS_NET_MAX_BATCH, RMS_NET_NBINS, RMS_NET_NIN, RMS_NET_NPARAMS, RMS_NET_PARAMS,

@@ -22,7 +22,8 @@ RMS_AXIS_LAMBDA2, RMS_AXIS_FREQ_HZ = 0, 1
 RMS_CHAN_MAJOR, RMS_LOS_MAJOR = 0, 1
 RMS_FP32_SIMT_FLY, RMS_FP32_SIMT_TABLE, RMS_BF16, RMS_BF16X3, RMS_FP16X3, RMS_FP32_CHIRPZ = range(6)
 (RMS_INFO_NCHAN, RMS_INFO_NCHAN_ACTIVE, RMS_INFO_NPHI, RMS_INFO_PRECISION, RMS_INFO_KPAD,
- RMS_INFO_NPAD, RMS_INFO_TILE_N, RMS_INFO_DEVICE) = range(8)
+ RMS_INFO_NPAD, RMS_INFO_TILE_N, RMS_INFO_DEVICE, RMS_INFO_LAST_CTAS, RMS_INFO_LAST_PAIR, RMS_INFO_LAST_PANELS,
+ RMS_INFO_LAST_KERNELS) = range(12)
 RMS_GET_LAMBDA2, RMS_GET_ACTIVE, RMS_GET_TABLE, RMS_GET_B_HI, RMS_GET_B_LO, RMS_GET_RMSF64 = range(6)
 
 PRECISIONS = {"fp32_fly": RMS_FP32_SIMT_FLY, "fp32_table": RMS_FP32_SIMT_TABLE, "bf16": RMS_BF16,

@@ -345,6 +345,15 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
             free_plan(p);
             return RMS_ERR_CUDA;
         }
+        // half-tile boxes for the two-CTA contraction (tile_n a multiple of 16, so a
+        // half is whole 8-row swizzle groups)
+        if (p->tile_n % 16 == 0 && p->tile_n_last % 16 == 0) {
+            const int h = p->tile_n / 2;
+            p->pair_maps = encode_b_map(&p->tmap2_bhi, p->d_bhi, p->kpad, p->npad, h) &&
+                           encode_b_map(&p->tmap2_blo, p->d_blo, p->kpad, p->npad, h) &&
+                           encode_b_map(&p->tmap2_bhi_raw, p->d_bhi_raw, p->kpad_raw, p->npad, h) &&
+                           encode_b_map(&p->tmap2_blo_raw, p->d_blo_raw, p->kpad_raw, p->npad, h);
+        }
     }
     RMS_TRY(cudaEventCreateWithFlags(&p->last, cudaEventDisableTiming));
     // rms_synth_noalloc on this plan must find its array and kernels loaded on the device
@@ -446,10 +455,12 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
     case RMS_BF16X3:
     case RMS_FP16X3: {
         // the split operand (and FP16X3's per-LOS exponents): stream-ordered scratch
+        // and 8 bytes of peak key per LOS (the contraction's split schedule)
         const size_t abytes = split_operand_bytes(*p, nlos, layout);
         const size_t rbytes = p->precision == RMS_FP16X3 ? (size_t)((nlos + 255) & ~(int64_t)255) : 0;
+        const size_t kbytes = (size_t)((nlos * 8 + 255) & ~(int64_t)255);
         uint8_t *scr = nullptr;
-        e = cudaMallocAsync(reinterpret_cast<void **>(&scr), abytes + rbytes, s);
+        e = cudaMallocAsync(reinterpret_cast<void **>(&scr), abytes + rbytes + kbytes, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return from_cuda(e);
@@ -468,7 +479,8 @@ static rms_status synth_launch(rms_plan_t p, const float *Q, const float *U, int
             cudaGetLastError();
         }
         e = launch_split_gemm(*p, Q, U, nlos, layout, F, pidx, pabs, pphi, scr,
-                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s, ev[1], x.q, x.u, x.chi);
+                              rbytes ? reinterpret_cast<int8_t *>(scr + abytes) : nullptr, s, ev[1], x.q, x.u, x.chi,
+                              reinterpret_cast<unsigned long long *>(scr + abytes + rbytes));
         if (ev[2]) {
             if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
             p->tev.insert(p->tev.end(), ev, ev + 3);
@@ -703,6 +715,10 @@ rms_status rms_plan_info(rms_plan_t p, int32_t what, int64_t *value)
     case RMS_INFO_NPAD: *value = p->npad; break;
     case RMS_INFO_TILE_N: *value = p->tile_n; break;
     case RMS_INFO_DEVICE: *value = p->device; break;
+    case RMS_INFO_LAST_CTAS: *value = p->last_ctas; break;
+    case RMS_INFO_LAST_PAIR: *value = p->last_pair; break;
+    case RMS_INFO_LAST_PANELS: *value = p->last_panels; break;
+    case RMS_INFO_LAST_KERNELS: *value = p->last_kernels; break;
     default: return RMS_ERR_INVALID_ARG;
     }
     return RMS_OK;

@@ -19,6 +19,16 @@
 //   warp 2      L2 prefetch of the next M tile's operand
 //   warps 4-11  epilogue: warp w owns TMEM lane quarter w % 4 and column half
 //               (w - 4) / 4; folds partials, scales, peak, stores F  -> tempty
+// The PAIR variant runs on clusters of two CTAs (two SMs) with tcgen05's
+// cta_group::2: every MMA is 256 rows (two M tiles, one per CTA) by tile_n, and
+// each CTA's shared memory holds its own 128 A rows and half of the B tile
+// (tile_n / 2 phase rows), so a stage carries half the phase-matrix bytes of the
+// single-CTA kernel for the same MMA work.  Every CTA loads its own stage and
+// waits for it on its own barrier; in the odd CTA warp 1 relays each filled
+// stage to the even CTA (a cluster-scope arrive), whose warp 1 issues the MMAs
+// once both halves are in.  Commits go to the barriers of both CTAs (multicast),
+// and the epilogue warps of both CTAs release a TMEM partial on the even CTA's
+// barrier.
 // MMAs run in groups of a few K blocks into one of two TMEM partials and the
 // epilogue folds each partial into FP32 registers with round-to-nearest adds,
 // because the tensor core's own FP32 accumulation does not round to nearest.
@@ -283,6 +293,15 @@ struct GemmParams {
     int *err;
     int64_t timeout_ns;
     int32_t stages;
+    // schedule: jobs_split = 0: one job per M tile (or M-tile pair) covering every N
+    // tile, peaks written directly; 1: one job per (N panel, M tile, N tile), ordered
+    // panel by panel, M tile by M tile, and dealt round-robin to the persistent CTAs,
+    // so that the CTAs working at any moment share a few M tiles' operands and one
+    // panel of the phase matrix in L2; each job's per-row peak goes into keys[row]
+    // with a 64-bit atomicMax and peak_finalize_kernel writes the peak outputs
+    int32_t jobs_split, npanels;
+    unsigned long long *keys;
+    int32_t b_rows;             // phase rows of a B stage in this CTA's shared memory (tile_n, or tile_n / 2 in pairs)
     int32_t prefetch;           // L2 prefetch of the next M tile's operand
     // window rotation (rotating kernel only): row r's operand is multiplied by
     // T[clamp(centre[r], cmin, cmax)][channel] before it enters the MMA
@@ -291,11 +310,11 @@ struct GemmParams {
     int32_t ldT, cmin, cmax;
 };
 
-// One pipeline stage: the A part(s) then the B part(s); 1024-byte multiples.
-__host__ __device__ __forceinline__ uint32_t gemm_stage_bytes(int tile_n, int mode)
+// One pipeline stage: the A part(s) then the B part(s) of b_rows phase rows each.
+__host__ __device__ __forceinline__ uint32_t gemm_stage_bytes(int b_rows, int mode)
 {
     const uint32_t parts = mode == MODE_BF16 ? 1u : 2u;
-    return parts * kStageA + parts * (uint32_t)tile_n * kRowBytes;
+    return parts * kStageA + parts * (uint32_t)b_rows * kRowBytes;
 }
 
 struct GSmem {
@@ -303,7 +322,7 @@ struct GSmem {
     uint32_t stage_bytes;
     float *epi, *pk_m, *pk_re, *pk_im;
     int *pk_i;
-    uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;
+    uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;   // conv: pair relay in PAIR
     uint32_t *tmem_slot;
     volatile int *abort_flag;
     volatile int *mt_started;   // M tiles the producer has started (read by the L2 prefetcher)
@@ -312,7 +331,7 @@ struct GSmem {
 __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
 {
     GSmem s;
-    s.stage_bytes = gemm_stage_bytes(P.tile_n, P.mode);
+    s.stage_bytes = gemm_stage_bytes(P.b_rows, P.mode);
     s.ring = base;
     s.epi = reinterpret_cast<float *>(s.ring + (size_t)P.stages * s.stage_bytes);
     s.pk_m = s.epi + kEpiStageBytes / 4;
@@ -336,34 +355,72 @@ __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
 
 constexpr int kConvWarp0 = 12;   // rotating kernel: warps 12-15 rotate the A operand in place
 
+// Job j of the schedule -> (work item it: an M tile, or an M-tile pair; N tiles [nt0, nt1)).
+__device__ __forceinline__ void job_of(const GemmParams &P, int64_t nit, int64_t j, int64_t &it, int &nt0, int &nt1)
+{
+    if (!P.jobs_split) {
+        it = j;
+        nt0 = 0;
+        nt1 = P.ntiles_n;
+        return;
+    }
+    // panel p holds N tiles [p ntiles_n / npanels, (p + 1) ntiles_n / npanels) and the
+    // jobs nit x (those tiles), M-major
+    int lo = 0, hi = P.ntiles_n;
+    for (int p = 0; p < P.npanels; ++p) {
+        lo = (int)((int64_t)p * P.ntiles_n / P.npanels);
+        hi = (int)((int64_t)(p + 1) * P.ntiles_n / P.npanels);
+        if (j < nit * hi) break;
+    }
+    const int64_t r = j - nit * lo;
+    const int len = hi - lo;
+    it = r / len;
+    nt0 = lo + (int)(r % len);
+    nt1 = nt0 + 1;
+}
+
 // HALF: columns of the tile per epilogue thread (tile_n <= 2 HALF).  ROT: the
 // window variant, 512 threads, whose converter warps rotate each stage's A
-// rows in shared memory before the MMA reads them.
-template <int HALF, bool ROT>
+// rows in shared memory before the MMA reads them.  PAIR: the two-CTA variant
+// (launched in clusters of two; not combined with ROT).
+template <int HALF, bool ROT, bool PAIR>
 __global__ void __launch_bounds__(ROT ? 512 : kThreads, 1)
 gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtensorMap tmB_hi,
             const __grid_constant__ CUtensorMap tmB_lo)
 {
+    static_assert(!(ROT && PAIR), "the rotating variant is single-CTA");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const GSmem S = gcarve(base, P);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nlos = P.count ? min(*P.count, P.nlos) : P.nlos;
     const int64_t nmt = (nlos + kTileM - 1) / kTileM;
+    // work items: M tiles, or pairs of M tiles (even tile in the even CTA)
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const int64_t nit = PAIR ? (nmt + 1) / 2 : nmt;
+    const int64_t it0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+    const int64_t istride = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+    const int64_t njobs = P.jobs_split ? nit * P.ntiles_n : nit;
     const bool split = P.mode != MODE_BF16;
     const int ngroups = (P.kblocks + P.group - 1) / P.group;
     const uint32_t a_bytes = split ? 2 * kStageA : kStageA;
-    const uint32_t b_bytes = (uint32_t)P.tile_n * kRowBytes;
+    const uint32_t b_bytes = (uint32_t)P.b_rows * kRowBytes;
+    // a wait that gives up in one CTA of a pair also stops the other one
+    const uint32_t peer_abort = PAIR ? mapa_shared(smem_u32((const void *)S.abort_flag), rank ^ 1u) : 0u;
+    auto stop_peer = [&]() {
+        if constexpr (PAIR) st_cluster_u32(peer_abort, 1u);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.stages; ++s) {
             mbar_init(smem_u32(&S.full[s]), 1);
             mbar_init(smem_u32(&S.empty[s]), 1);
-            mbar_init(smem_u32(&S.conv[s]), 4);
+            mbar_init(smem_u32(&S.conv[s]), PAIR ? 1 : 4);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.tfull[b]), 1);
-            mbar_init(smem_u32(&S.tempty[b]), kNumEpiWarps);
+            mbar_init(smem_u32(&S.tempty[b]), PAIR ? 2 * kNumEpiWarps : kNumEpiWarps);
         }
         for (int i = 0; i < 8; ++i) {
             mbar_init(smem_u32(&S.pkfull[i]), 1);
@@ -376,10 +433,12 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
     }
     if (warp == 1) {
         __syncwarp();
-        tmem_alloc(smem_u32(S.tmem_slot), kTmemCols);
+        if constexpr (PAIR) tmem_alloc_pair(smem_u32(S.tmem_slot), kTmemCols);
+        else tmem_alloc(smem_u32(S.tmem_slot), kTmemCols);
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();   // the peer's barriers exist before anything targets them
     tc_fence_after();
     const uint32_t tmem_base = *S.tmem_slot;
 
@@ -393,10 +452,17 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             uint32_t ph = 0, pending = 0, pend_par = 0;
             bool ok = true;
             int mt_count = 0;
-            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count) {
+            for (int64_t j = it0; j < njobs && ok; j += istride, ++mt_count) {
+                int64_t it;
+                int nt0, nt1;
+                job_of(P, nit, j, it, nt0, nt1);
+                const int64_t mt = PAIR ? 2 * it + rank : it;
                 *S.mt_started = mt_count + 1;
                 const uint8_t *a_mt = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
-                for (int nt = 0; nt < P.ntiles_n && ok; ++nt)
+                for (int nt = nt0; nt < nt1 && ok; ++nt) {
+                    // phase rows of this CTA's part of the tile: all of it, or the pair's half
+                    int32_t y = nt * P.tile_n;
+                    if (PAIR && !leader) y += ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) / 2;
                     for (int kb = 0; kb < P.kblocks; ++kb) {
                         if (!wait_bounded(smem_u32(&S.empty[s]), ph ^ 1, S.abort_flag, P.err, P.timeout_ns)) {
                             ok = false;
@@ -406,35 +472,81 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                         const uint32_t bar = smem_u32(&S.full[s]);
                         mbar_arrive_expect_tx(bar, tx);
                         bulk_load(st, a_mt + (size_t)kb * (2 * kStageA), a_bytes, bar);
-                        tma_load_2d(st + a_bytes, &tmB_hi, kb * kKBlock, nt * P.tile_n, bar);
-                        if (split) tma_load_2d(st + a_bytes + b_bytes, &tmB_lo, kb * kKBlock, nt * P.tile_n, bar);
+                        tma_load_2d(st + a_bytes, &tmB_hi, kb * kKBlock, y, bar);
+                        if (split) tma_load_2d(st + a_bytes + b_bytes, &tmB_lo, kb * kKBlock, y, bar);
                         pending |= 1u << s;
                         pend_par = (pend_par & ~(1u << s)) | (ph << s);
                         if (++s == P.stages) { s = 0; ph ^= 1; }
                     }
+                }
             }
-            if (!ok)
+            if (!ok) {
+                stop_peer();
                 for (int i = 0; i < P.stages; ++i)
                     if (pending & (1u << i))
                         wait_bounded(smem_u32(&S.full[i]), (pend_par >> i) & 1, S.abort_flag, P.err, P.timeout_ns,
                                      false);
+            } else if (PAIR) {
+                // the MMAs' commits arrive on this CTA's barriers from the tensor core: wait
+                // for the one that releases each slot's last fill before the CTA may exit
+                for (int i = 0; i < P.stages; ++i)
+                    if ((pending & (1u << i)) &&
+                        !wait_bounded(smem_u32(&S.empty[i]), (pend_par >> i) & 1, S.abort_flag, P.err,
+                                      P.timeout_ns)) {
+                        stop_peer();
+                        break;
+                    }
+            }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (PAIR && !leader) {
+            // -------------------------------------------------------- pair relay (odd CTA)
+            // every stage this CTA filled is announced to the even CTA's MMA issuer
+            if (lane == 0) {
+                int s = 0;
+                uint32_t ph = 0;
+                bool ok = true;
+                for (int64_t j = it0; j < njobs && ok; j += istride) {
+                    int64_t it;
+                    int nt0, nt1;
+                    job_of(P, nit, j, it, nt0, nt1);
+                    for (int nt = nt0; nt < nt1 && ok; ++nt)
+                        for (int kb = 0; kb < P.kblocks; ++kb) {
+                            if (!wait_bounded(smem_u32(&S.full[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_cluster(mapa_shared(smem_u32(&S.conv[s]), 0u));
+                            if (++s == P.stages) { s = 0; ph ^= 1; }
+                        }
+                }
+                if (!ok) stop_peer();
+                // the even CTA's last commit: all MMAs that touch this CTA are complete
+                else if (!wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns))
+                    stop_peer();
+            }
+        } else if (lane == 0) {
+            // -------------------------------------------------------- MMA issuer
             const bool bf = P.mode != MODE_FP16X3;
-            const uint32_t id_full = idesc_f16(P.tile_n, bf), id_last = idesc_f16(P.tile_n_last, bf);
+            const int mrows = PAIR ? 2 * kTileM : kTileM;
+            const uint32_t id_full = idesc_f16_m(mrows, P.tile_n, bf), id_last = idesc_f16_m(mrows, P.tile_n_last, bf);
             int s = 0;
             uint32_t ph = 0, tph = 0;
             int g_all = 0;
             bool ok = true, issued = false;
-            for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x)
-                for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
+            for (int64_t j = it0; j < njobs && ok; j += istride) {
+                int64_t it;
+                int nt0, nt1;
+                job_of(P, nit, j, it, nt0, nt1);
+                for (int nt = nt0; nt < nt1 && ok; ++nt) {
                     const uint32_t idesc = (nt == P.ntiles_n - 1) ? id_last : id_full;
                     for (int g = 0; g < ngroups && ok; ++g, ++g_all) {
                         const int b = g_all & 1;
-                        if (!wait_bounded(smem_u32(&S.tempty[b]), ((tph >> b) & 1) ^ 1, S.abort_flag, P.err,
-                                          P.timeout_ns)) {
+                        const bool got = PAIR ? wait_bounded_cluster(smem_u32(&S.tempty[b]), ((tph >> b) & 1) ^ 1,
+                                                                     S.abort_flag, P.err, P.timeout_ns)
+                                              : wait_bounded(smem_u32(&S.tempty[b]), ((tph >> b) & 1) ^ 1,
+                                                             S.abort_flag, P.err, P.timeout_ns);
+                        if (!got) {
                             ok = false;
                             break;
                         }
@@ -443,7 +555,9 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                         const int kb0 = g * P.group, kb1 = min(P.kblocks, kb0 + P.group);
                         for (int kb = kb0; kb < kb1; ++kb) {
                             const uint64_t *ready = ROT ? &S.conv[s] : &S.full[s];
-                            if (!wait_bounded(smem_u32(ready), ph, S.abort_flag, P.err, P.timeout_ns)) {
+                            if (!wait_bounded(smem_u32(ready), ph, S.abort_flag, P.err, P.timeout_ns) ||
+                                (PAIR && !wait_bounded_cluster(smem_u32(&S.conv[s]), ph, S.abort_flag, P.err,
+                                                               P.timeout_ns))) {
                                 ok = false;
                                 break;
                             }
@@ -455,22 +569,38 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                             for (int kk = 0; kk < kKBlock / 16; ++kk) {
                                 const uint32_t ko = kk * 32;
                                 const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-                                mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_hi + ko), idesc, acc);
-                                if (split) {
-                                    mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_lo + ko), idesc, 1u);
-                                    mma_f16(d, sdesc_k64(a_lo + ko), sdesc_k64(b_hi + ko), idesc, 1u);
+                                if constexpr (PAIR) {
+                                    mma_f16_pair(d, sdesc_k64(a_hi + ko), sdesc_k64(b_hi + ko), idesc, acc);
+                                    if (split) {
+                                        mma_f16_pair(d, sdesc_k64(a_hi + ko), sdesc_k64(b_lo + ko), idesc, 1u);
+                                        mma_f16_pair(d, sdesc_k64(a_lo + ko), sdesc_k64(b_hi + ko), idesc, 1u);
+                                    }
+                                } else {
+                                    mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_hi + ko), idesc, acc);
+                                    if (split) {
+                                        mma_f16(d, sdesc_k64(a_hi + ko), sdesc_k64(b_lo + ko), idesc, 1u);
+                                        mma_f16(d, sdesc_k64(a_lo + ko), sdesc_k64(b_hi + ko), idesc, 1u);
+                                    }
                                 }
                             }
                             issued = true;
-                            mma_commit(smem_u32(&S.empty[s]));
+                            if constexpr (PAIR) mma_commit_pair_mc(smem_u32(&S.empty[s]), (uint16_t)3);
+                            else mma_commit(smem_u32(&S.empty[s]));
                             if (++s == P.stages) { s = 0; ph ^= 1; }
                         }
                         if (!ok) break;
-                        mma_commit(smem_u32(&S.tfull[b]));
+                        if constexpr (PAIR) mma_commit_pair_mc(smem_u32(&S.tfull[b]), (uint16_t)3);
+                        else mma_commit(smem_u32(&S.tfull[b]));
                         tph ^= 1u << b;
                     }
                 }
-            if (issued) {
+            }
+            if (!ok) stop_peer();
+            if constexpr (PAIR) {
+                // both CTAs wait for this commit before they leave (the odd CTA in its relay)
+                mma_commit_pair_mc(smem_u32(S.mma_done), (uint16_t)3);
+                wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
+            } else if (issued) {
                 mma_commit(smem_u32(S.mma_done));
                 wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
             }
@@ -482,7 +612,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         // A performance hint only: on a stall or an abort it stops.
         const size_t blk = (size_t)P.kblocks * (2 * kStageA);
         int mt_count = 0;
-        for (int64_t mt = blockIdx.x; P.prefetch && mt + gridDim.x < nmt; mt += gridDim.x, ++mt_count) {
+        for (int64_t mt = blockIdx.x; !PAIR && P.prefetch && !P.jobs_split && mt + gridDim.x < nmt;
+             mt += gridDim.x, ++mt_count) {
             const uint64_t t0 = global_ns();
             bool go = true;
             while (go && *S.mt_started < mt_count + 1) {
@@ -563,13 +694,21 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         int g_all = 0, mt_count = 0;
         bool ok = true;
         float master[HALF];
-        for (int64_t mt = blockIdx.x; mt < nmt && ok; mt += gridDim.x, ++mt_count) {
+        // the even CTA's barrier that releases a TMEM partial (this CTA's own without pairs)
+        uint32_t tempty_addr[2];
+        for (int b = 0; b < 2; ++b)
+            tempty_addr[b] = PAIR ? mapa_shared(smem_u32(&S.tempty[b]), 0u) : smem_u32(&S.tempty[b]);
+        for (int64_t j = it0; j < njobs && ok; j += istride, ++mt_count) {
+            int64_t it;
+            int nt0, nt1;
+            job_of(P, nit, j, it, nt0, nt1);
+            const int64_t mt = PAIR ? 2 * it + rank : it;
             const int64_t row = mt * kTileM + 32 * q + lane;
             float scale = P.out_scale;
             if (P.rexp != nullptr && row < nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
             float bm = -1.0f, br = 0.f, bim = 0.f;
             int bi = INT_MAX;
-            for (int nt = 0; nt < P.ntiles_n && ok; ++nt) {
+            for (int nt = nt0; nt < nt1 && ok; ++nt) {
                 for (int g = 0; g < ngroups; ++g, ++g_all) {
                     const int b = g_all & 1;
                     if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) {
@@ -598,7 +737,10 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&S.tempty[b]));
+                    if (lane == 0) {
+                        if constexpr (PAIR) mbar_arrive_cluster(tempty_addr[b]);
+                        else mbar_arrive(tempty_addr[b]);
+                    }
                 }
                 if (!ok) break;
                 const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * HALF;
@@ -670,7 +812,14 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 __syncwarp();
                 if (lane == 0) mbar_arrive(ebar);
                 if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; br = ore; bim = oim; }
-                if (row < nlos) {
+                if (P.jobs_split) {
+                    // this job's peak of the row: |F|^2 bits (monotonic for values >= 0) above
+                    // the complement of the index, so the largest key is the largest |F|^2
+                    // with the lowest index among equal ones; NaN never gets here
+                    if (row < nlos && bi != INT_MAX)
+                        atomicMax(P.keys + row, ((unsigned long long)__float_as_uint(bm) << 32) |
+                                                    (unsigned long long)(0xFFFFFFFFu - (uint32_t)bi));
+                } else if (row < nlos) {
                     const int64_t orow = P.rows ? P.rows[row] : row;
                     const bool found = bi != INT_MAX;
                     if (P.pidx) P.pidx[orow] = found ? bi : -1;
@@ -693,23 +842,75 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         }
     }
 
+    if constexpr (PAIR) {
+        if (*S.abort_flag) stop_peer();
+    }
     tc_fence_before();
     __syncthreads();
+    // in a pair, neither CTA leaves (or frees TMEM) while the other may still use its
+    // shared memory, barriers or TMEM
+    if constexpr (PAIR) cluster_sync_all();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem_base, kTmemCols);
+        if constexpr (PAIR) tmem_dealloc_pair(tmem_base, kTmemCols);
+        else tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// Peak outputs from the merged keys of the split schedule (one thread per image
+// row): the same values the contraction's epilogue writes in the whole schedule --
+// index, sqrt of the FP32 |F|^2, phi, and Re F, Im F and chi0 read back from the
+// stored F at the peak.
+__global__ void peak_finalize_kernel(const unsigned long long *__restrict__ keys, int64_t n, const int64_t *count,
+                                     const int64_t *rows, const float *F, int32_t nphi, const float *phi32,
+                                     const double *phi64, double lambda0sq, int32_t *pidx, float *pabs, float *pphi,
+                                     float *pq, float *pu, float *pchi)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_eff = count ? min(*count, n) : n;
+    if (r >= n_eff) return;
+    const unsigned long long key = keys[r];
+    const int64_t orow = rows ? rows[r] : r;
+    const bool found = key != 0ull;
+    const int bi = found ? (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
+    const float bm = __uint_as_float((uint32_t)(key >> 32));
+    const float nan = __int_as_float(0x7fc00000);
+    if (pidx) pidx[orow] = bi;
+    if (pabs) pabs[orow] = found ? sqrtf(bm) : nan;
+    if (pphi) pphi[orow] = found ? phi32[bi] : nan;
+    if (pq || pu || pchi) {
+        float br = nan, bim = nan;
+        if (found) {
+            const float2 v = *reinterpret_cast<const float2 *>(F + orow * 2 * (int64_t)nphi + 2 * (int64_t)bi);
+            br = v.x;
+            bim = v.y;
+        }
+        if (pq) pq[orow] = br;
+        if (pu) pu[orow] = bim;
+        if (pchi) {
+            // chi0 = arg F(phi_peak) / 2 - phi_peak lambda_0^2, reduced to [0, pi)
+            float c = nan;
+            if (found) {
+                double x = 0.5 * atan2((double)bim, (double)br) - phi64[bi] * lambda0sq;
+                x -= M_PI * floor(x / M_PI);
+                c = (float)x;
+            }
+            pchi[orow] = c;
+        }
     }
 }
 
 size_t gemm_fixed_smem() { return 1024 + kEpiStageBytes + 2 * 4 * 32 * 16 + 8 * 32 + 32; }
 
-int gemm_stages(int tile_n, int mode)
+int gemm_stages(int b_rows, int mode)
 {
-    size_t st = gemm_stage_bytes(tile_n, mode);
+    size_t st = gemm_stage_bytes(b_rows, mode);
     int s = (int)((kSmemLimit - gemm_fixed_smem()) / (st + 24));
     return s > 8 ? 8 : s;
 }
+
+bool split_mode(int mode) { return mode != MODE_BF16; }
 
 int mode_of(int precision)
 {
@@ -720,8 +921,11 @@ int mode_of(int precision)
 
 size_t split_operand_bytes(const rms_plan_s &p, int64_t nlos, int layout)
 {
+    // an even number of M tiles: the two-CTA contraction reads M tiles in pairs (the
+    // rows of a padding tile only ever reach rows of the result that are not stored)
     const int kb = layout == RMS_CHAN_MAJOR ? p.kblocks : p.kblocks_raw;
-    return (size_t)((nlos + kTileM - 1) / kTileM) * kb * (2 * kStageA);
+    const int64_t nmt = (nlos + kTileM - 1) / kTileM;
+    return (size_t)((nmt + 1) & ~(int64_t)1) * kb * (2 * kStageA);
 }
 
 cudaError_t launch_split(const rms_plan_s &p, const SplitOpts &o, cudaStream_t s)
@@ -801,7 +1005,6 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.rexp = mode == MODE_FP16X3 ? o.rexp : nullptr;
     P.err = p.d_err;
     P.timeout_ns = p.timeout_ns;
-    P.stages = gemm_stages(p.tile_n, mode);
     P.centre = o.centre;
     P.T = o.T;
     P.ldT = o.ldT;
@@ -814,29 +1017,139 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         return (v && v[0] == '1') ? 1 : 0;
     }();
     P.prefetch = prefetch;
+    // the two-CTA contraction serves every full-grid call; RMS_GEMM_PAIR=0 selects the
+    // single-CTA kernel instead (a measurement switch: both compute the same sums)
+    static const bool pair_ok = [] {
+        const char *v = std::getenv("RMS_GEMM_PAIR");
+        return !(v && v[0] == '0');
+    }();
+    const bool pair = !rot && pair_ok && p.pair_maps;
+    P.b_rows = pair ? p.tile_n / 2 : p.tile_n;
+    P.stages = gemm_stages(P.b_rows, mode);
     if (P.stages < 2) return cudaErrorInvalidConfiguration;
-    size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(p.tile_n, mode) + 24 * (size_t)P.stages;
+    size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(P.b_rows, mode) + 24 * (size_t)P.stages;
     int ctas = p.num_sms;
     if (const char *v = std::getenv("RMS_GEMM_CTAS")) {   // tuning knob: persistent CTAs
         int c = std::atoi(v);
         if (c >= 1 && c <= p.num_sms) ctas = c;
     }
-    int grid = (int)(nmt < ctas ? nmt : ctas);
-    const CUtensorMap &bhi = chan ? p.tmap_bhi : p.tmap_bhi_raw, &blo = chan ? p.tmap_blo : p.tmap_blo_raw;
+    const int64_t nit = pair ? (nmt + 1) / 2 : nmt;
+    int maxunits = pair ? (ctas / 2 > 0 ? ctas / 2 : 1) : ctas;
+    if (pair) {
+        // a pair needs two SMs of one TPC; TPCs with a disabled SM cannot host one, so
+        // the persistent grid takes as many clusters as can be resident at once (more
+        // would wait for a second wave)
+        cudaError_t e0 = cudaFuncSetAttribute(gemm_kernel<kHalf, false, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e0 != cudaSuccess) return e0;
+        cudaLaunchConfig_t qc = {};
+        qc.gridDim = dim3((unsigned)(2 * maxunits), 1, 1);
+        qc.blockDim = dim3(kThreads, 1, 1);
+        qc.dynamicSmemBytes = smem;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = 2;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        qc.attrs = qa;
+        qc.numAttrs = 1;
+        int nclusters = 0;
+        e0 = cudaOccupancyMaxActiveClusters(&nclusters, gemm_kernel<kHalf, false, true>, &qc);
+        if (e0 != cudaSuccess) return e0;
+        if (nclusters < 1) return cudaErrorInvalidConfiguration;
+        if (nclusters < maxunits) maxunits = nclusters;
+    }
+    const int units = (int)(nit < maxunits ? nit : maxunits);
+    // Schedule.  Whole: every CTA (pair) runs all N tiles of its M tile(s), re-reading
+    // their operand once per N tile; those re-reads hit L2 only while the operands of
+    // all M tiles in flight plus the whole phase matrix fit there.  Otherwise split:
+    // single-N-tile jobs in panels (see GemmParams), with the smallest number of
+    // panels whose working set -- the operands of the M tiles the CTAs share at one
+    // time plus one panel of the phase matrix -- fits the budget.  RMS_L2_BUDGET_MB
+    // (8 .. 1024) overrides the 80 MB budget (a tuning knob).
+    static const double budget = [] {
+        const char *v = std::getenv("RMS_L2_BUDGET_MB");
+        const int mb = v ? std::atoi(v) : 0;
+        return (mb >= 8 && mb <= 1024 ? mb : 80) * 1048576.0;
+    }();
+    P.jobs_split = 0;
+    P.npanels = 1;
+    P.keys = nullptr;
+    const bool f_at_peak = o.pq || o.pu || o.pchi;
+    if (!rot && o.keys && (o.F || !f_at_peak)) {
+        const double tiles_per_unit = pair ? 2.0 : 1.0;
+        const double a_tile = (double)P.kblocks * (split_mode(mode) ? 2 * kStageA : kStageA);
+        const double b_all = (double)p.npad * (chan ? p.kpad : p.kpad_raw) * 2.0 * (split_mode(mode) ? 2 : 1);
+        const double whole = units * tiles_per_unit * a_tile + b_all;
+        if (whole > budget) {
+            int best = 1;
+            double best_live = 1e300;
+            for (int np = 1; np <= p.ntiles_n; ++np) {
+                const int len = p.ntiles_n / np;
+                const double live = ((units + len - 1) / len + 1) * tiles_per_unit * a_tile + b_all / np;
+                if (live <= budget) { best = np; best_live = live; break; }
+                if (live < best_live) { best = np; best_live = live; }
+            }
+            P.jobs_split = 1;
+            P.npanels = best;
+            P.keys = o.keys;
+        }
+    }
     cudaError_t e;
+    if (P.jobs_split) {
+        e = cudaMemsetAsync(P.keys, 0, (size_t)o.nlos * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
     if (rot) {
-        auto kern = gemm_kernel<kHalfRot, true>;
+        const CUtensorMap &bhi = chan ? p.tmap_bhi : p.tmap_bhi_raw, &blo = chan ? p.tmap_blo : p.tmap_blo_raw;
+        auto kern = gemm_kernel<kHalfRot, true, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, 512, smem, s>>>(P, bhi, blo);
+        kern<<<units, 512, smem, s>>>(P, bhi, blo);
+    } else if (pair) {
+        if (p.tile_n > 2 * kHalf || (p.tile_n & 15) || (p.tile_n_last & 15)) return cudaErrorInvalidValue;
+        const CUtensorMap &bhi = chan ? p.tmap2_bhi : p.tmap2_bhi_raw, &blo = chan ? p.tmap2_blo : p.tmap2_blo_raw;
+        const int pairs = units;
+        auto kern = gemm_kernel<kHalf, false, true>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, kern, P, bhi, blo);
+        if (e != cudaSuccess) return e;
     } else {
         if (p.tile_n > 2 * kHalf) return cudaErrorInvalidValue;
-        auto kern = gemm_kernel<kHalf, false>;
+        const CUtensorMap &bhi = chan ? p.tmap_bhi : p.tmap_bhi_raw, &blo = chan ? p.tmap_blo : p.tmap_blo_raw;
+        auto kern = gemm_kernel<kHalf, false, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, kThreads, smem, s>>>(P, bhi, blo);
+        kern<<<units, kThreads, smem, s>>>(P, bhi, blo);
     }
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    p.last_ctas = pair ? 2 * units : units;
+    p.last_pair = pair ? 1 : 0;
+    p.last_panels = P.jobs_split ? P.npanels : 0;
+    p.last_kernels = 1;
+    if (P.jobs_split && (o.pidx || o.pabs || o.pphi || f_at_peak)) {
+        p.last_kernels = 2;
+        const int64_t nb = (o.nlos + 255) / 256;
+        if (nb > 0x7fffffff) return cudaErrorInvalidValue;
+        peak_finalize_kernel<<<(unsigned)nb, 256, 0, s>>>(P.keys, o.nlos, o.count, o.rows, o.F, p.nphi, p.d_phi32,
+                                                          p.d_phi, p.lambda0sq, o.pidx, o.pabs, o.pphi, o.pq, o.pu,
+                                                          o.pchi);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *src, const int64_t *rows,
@@ -854,7 +1167,8 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
 
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
-                              cudaStream_t s, cudaEvent_t ev_mid, float *pq, float *pu, float *pchi)
+                              cudaStream_t s, cudaEvent_t ev_mid, float *pq, float *pu, float *pchi,
+                              unsigned long long *keys)
 {
     SplitOpts so;
     so.Q = Q;
@@ -879,5 +1193,8 @@ cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *
     go.pu = pu;
     go.pchi = pchi;
     go.rexp = rexp;
-    return launch_gemm(p, go, s);
+    go.keys = keys;
+    e = launch_gemm(p, go, s);
+    p.last_kernels += 1;   // the split
+    return e;
 }

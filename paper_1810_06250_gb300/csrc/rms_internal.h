@@ -54,6 +54,10 @@ struct rms_plan_s {
     int32_t kpad_raw = 0, kblocks_raw = 0;
     CUtensorMap tmap_bhi_raw;
     CUtensorMap tmap_blo_raw;
+    // the same matrices in boxes of tile_n / 2 rows: each CTA of a two-CTA
+    // contraction loads its half of a tile
+    CUtensorMap tmap2_bhi, tmap2_blo, tmap2_bhi_raw, tmap2_blo_raw;
+    bool pair_maps = false;
 
     // sticky device error word, mapped host memory (readable without a sync)
     int *h_err = nullptr;
@@ -76,6 +80,11 @@ struct rms_plan_s {
     // FP16X3: per-LOS exponent scratch
     size_t rexp_cap = 0;
     int8_t *d_rexp = nullptr;
+
+    // what the last tensor-core synthesis call ran (rms_plan_info): persistent CTAs of
+    // the contraction, 1 if it ran as CTA pairs, N panels of the split schedule (0:
+    // whole schedule), kernels launched by the call
+    mutable int32_t last_ctas = 0, last_pair = 0, last_panels = 0, last_kernels = 0;
 
     // optional kernel timing (rms_plan_set_kernel_timing): events around the layout
     // stage and the contraction of each tensor-core synthesis call
@@ -146,6 +155,9 @@ struct GemmOpts {
     const int32_t *centre = nullptr;
     const float2 *T = nullptr;
     int32_t ldT = 0, cmin = 0, cmax = 0;
+    // optional scratch of nlos 64-bit peak keys: lets the contraction use its split
+    // schedule (needed on cubes whose operands do not stay in L2; see gemm.cu)
+    unsigned long long *keys = nullptr;
 };
 cudaError_t launch_split(const rms_plan_s &p, const SplitOpts &o, cudaStream_t s);
 cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s);
@@ -154,7 +166,7 @@ cudaError_t launch_image_gather(const rms_plan_s &p, int layout, const uint8_t *
 cudaError_t launch_split_gemm(const rms_plan_s &p, const float *Q, const float *U, int64_t nlos, int layout,
                               float *F, int32_t *pidx, float *pabs, float *pphi, uint8_t *A, int8_t *rexp,
                               cudaStream_t s, cudaEvent_t ev_mid = nullptr, float *pq = nullptr,
-                              float *pu = nullptr, float *pchi = nullptr);
+                              float *pu = nullptr, float *pchi = nullptr, unsigned long long *keys = nullptr);
 
 // generate.cu
 cudaError_t launch_generate(const rms_plan_s &p, const rms_source_model &m, int64_t los0, int64_t nlos,
