@@ -292,6 +292,28 @@ const char *rms_status_string(rms_status s);
 rms_status rms_plan_set_timeout(rms_plan_t plan, int64_t ns);
 
 /*
+ * How the tensor-core contraction of a plan is scheduled (no paper counterpart;
+ * for measurement and tuning -- none of these changes a result):
+ *   RMS_OPT_CONTRACTION  RMS_CONTRACT_AUTO (default): CTA pairs when the plan's
+ *                        tiles allow them; RMS_CONTRACT_SINGLE: one CTA per 128-row
+ *                        MMA; RMS_CONTRACT_PAIR: CTA pairs (256-row MMAs on two SMs,
+ *                        each SM holding half of the phase tile), or
+ *                        RMS_ERR_UNSUPPORTED when the tiles do not allow them.
+ *   RMS_OPT_L2_BUDGET    bytes of L2 the schedule may count on (0 = the default,
+ *                        80 MiB).  While the operands of the line-of-sight tiles in
+ *                        flight plus the whole phase matrix fit, every CTA runs all
+ *                        phase tiles of its lines of sight; otherwise it runs
+ *                        single-tile jobs in panels of the phase matrix and the peak
+ *                        map is merged afterwards.  Both give bit-identical outputs.
+ * The environment variables RMS_GEMM_PAIR=0 and RMS_L2_BUDGET_MB=<MiB>, read once
+ * per process, change the defaults of new plans.  Synchronous; RMS_ERR_INVALID_ARG
+ * for an unknown option or value.
+ */
+enum { RMS_OPT_CONTRACTION = 0, RMS_OPT_L2_BUDGET = 1 };
+enum { RMS_CONTRACT_AUTO = 0, RMS_CONTRACT_SINGLE = 1, RMS_CONTRACT_PAIR = 2 };
+rms_status rms_plan_set_option(rms_plan_t plan, int32_t option, int64_t value);
+
+/*
  * Kernel timing for measurement (the paper has no counterpart).  While enabled,
  * every tensor-core synthesis call on the plan records CUDA events on its
  * stream around its two kernels (the layout stage that splits the cube into

@@ -37,7 +37,7 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
            "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout", "rms_clean_create",
-           "rms_clean_destroy", "rms_clean", "rms_refine_peaks", "rms_window_centres")
+           "rms_clean_destroy", "rms_clean", "rms_refine_peaks", "rms_window_centres", "rms_plan_set_option")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
             "rms_plan_get": [P, _i32, P, _i64],
             "rms_plan_destroy": [P],
             "rms_plan_set_timeout": [P, _i64],
+            "rms_plan_set_option": [P, _i32, _i64],
             "rms_generate": [P, P, _i64, _i64, _i32, P, P, P],
             "rms_plan_set_kernel_timing": [P, _i32],
             "rms_synth_peaks": [P, P, P, _i64, _i32, P, P, P],
@@ -245,6 +246,14 @@ def rms_synth_host(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None
 
 def rms_plan_sync(plan: int, stream=None):
     _check(load().rms_plan_sync(plan, _stream(stream)), "rms_plan_sync")
+
+
+RMS_OPT_CONTRACTION, RMS_OPT_L2_BUDGET = 0, 1
+RMS_CONTRACT_AUTO, RMS_CONTRACT_SINGLE, RMS_CONTRACT_PAIR = 0, 1, 2
+
+
+def rms_plan_set_option(plan: int, option: int, value: int):
+    _check(load().rms_plan_set_option(plan, int(option), int(value)), "rms_plan_set_option")
 
 
 def rms_plan_set_timeout(plan: int, ns: int):

@@ -153,12 +153,12 @@ out:
 
 bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, void *base, const cuuint64_t *dims,
                        const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr,
-                       CUtensorMapSwizzle swizzle)
+                       CUtensorMapSwizzle swizzle, int rank)
 {
     auto enc = get_encode();
     if (!enc) return false;
-    CUresult r = enc(map, type, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(map, type, (cuuint32_t)rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -701,6 +701,23 @@ rms_status rms_plan_set_timeout(rms_plan_t p, int64_t ns)
     if (!p || ns <= 0) return RMS_ERR_INVALID_ARG;
     p->timeout_ns = ns;
     return RMS_OK;
+}
+
+rms_status rms_plan_set_option(rms_plan_t p, int32_t option, int64_t value)
+{
+    if (!p) return RMS_ERR_INVALID_ARG;
+    switch (option) {
+    case RMS_OPT_CONTRACTION:
+        if (value < RMS_CONTRACT_AUTO || value > RMS_CONTRACT_PAIR) return RMS_ERR_INVALID_ARG;
+        if (value == RMS_CONTRACT_PAIR && !p->pair_maps) return RMS_ERR_UNSUPPORTED;
+        p->contraction = (int32_t)value;
+        return RMS_OK;
+    case RMS_OPT_L2_BUDGET:
+        if (value < 0) return RMS_ERR_INVALID_ARG;
+        p->l2_budget = value;
+        return RMS_OK;
+    default: return RMS_ERR_INVALID_ARG;
+    }
 }
 
 rms_status rms_plan_info(rms_plan_t p, int32_t what, int64_t *value)

@@ -386,7 +386,7 @@ __device__ __forceinline__ void job_of(const GemmParams &P, int64_t nit, int64_t
 template <int HALF, bool ROT, bool PAIR>
 __global__ void __launch_bounds__(ROT ? 512 : kThreads, 1)
 gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtensorMap tmB_hi,
-            const __grid_constant__ CUtensorMap tmB_lo)
+            const __grid_constant__ CUtensorMap tmB_lo, const __grid_constant__ CUtensorMap tmA)
 {
     static_assert(!(ROT && PAIR), "the rotating variant is single-CTA");
     extern __shared__ uint8_t smem_raw[];
@@ -447,6 +447,9 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_hi)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB_lo)) : "memory");
+            if (PAIR) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            // bytes one CTA loads per stage; in a pair both CTAs' loads complete on the
+            // even CTA's full barrier, which alone expects them (twice this)
             const uint32_t tx = a_bytes + (split ? 2 * b_bytes : b_bytes);
             int s = 0;
             uint32_t ph = 0, pending = 0, pend_par = 0;
@@ -470,10 +473,18 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                         }
                         const uint32_t st = smem_u32(S.ring + (size_t)s * S.stage_bytes);
                         const uint32_t bar = smem_u32(&S.full[s]);
-                        mbar_arrive_expect_tx(bar, tx);
-                        bulk_load(st, a_mt + (size_t)kb * (2 * kStageA), a_bytes, bar);
-                        tma_load_2d(st + a_bytes, &tmB_hi, kb * kKBlock, y, bar);
-                        if (split) tma_load_2d(st + a_bytes + b_bytes, &tmB_lo, kb * kKBlock, y, bar);
+                        if constexpr (PAIR) {
+                            const uint32_t bar0 = mapa_shared(bar, 0u);
+                            if (leader) mbar_arrive_expect_tx(bar, 2 * tx);
+                            tma_load_3d_pair(st, &tmA, 0, 0, (int32_t)(mt * P.kblocks + kb), bar0);
+                            tma_load_2d_pair(st + a_bytes, &tmB_hi, kb * kKBlock, y, bar0);
+                            if (split) tma_load_2d_pair(st + a_bytes + b_bytes, &tmB_lo, kb * kKBlock, y, bar0);
+                        } else {
+                            mbar_arrive_expect_tx(bar, tx);
+                            bulk_load(st, a_mt + (size_t)kb * (2 * kStageA), a_bytes, bar);
+                            tma_load_2d(st + a_bytes, &tmB_hi, kb * kKBlock, y, bar);
+                            if (split) tma_load_2d(st + a_bytes + b_bytes, &tmB_lo, kb * kKBlock, y, bar);
+                        }
                         pending |= 1u << s;
                         pend_par = (pend_par & ~(1u << s)) | (ph << s);
                         if (++s == P.stages) { s = 0; ph ^= 1; }
@@ -482,10 +493,17 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             }
             if (!ok) {
                 stop_peer();
-                for (int i = 0; i < P.stages; ++i)
-                    if (pending & (1u << i))
-                        wait_bounded(smem_u32(&S.full[i]), (pend_par >> i) & 1, S.abort_flag, P.err, P.timeout_ns,
-                                     false);
+                if (!PAIR || leader) {
+                    for (int i = 0; i < P.stages; ++i)
+                        if (pending & (1u << i))
+                            wait_bounded(smem_u32(&S.full[i]), (pend_par >> i) & 1, S.abort_flag, P.err,
+                                         P.timeout_ns, false);
+                } else {
+                    // the odd CTA's copies complete on the even CTA's barriers: give any still in
+                    // flight far longer than a copy takes before this CTA may leave
+                    const uint64_t t0 = global_ns();
+                    while (global_ns() - t0 < 200000ull) __nanosleep(1000);
+                }
             } else if (PAIR) {
                 // the MMAs' commits arrive on this CTA's barriers from the tensor core: wait
                 // for the one that releases each slot's last fill before the CTA may exit
@@ -500,31 +518,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         }
     } else if (warp == 1) {
         if (PAIR && !leader) {
-            // -------------------------------------------------------- pair relay (odd CTA)
-            // every stage this CTA filled is announced to the even CTA's MMA issuer
-            if (lane == 0) {
-                int s = 0;
-                uint32_t ph = 0;
-                bool ok = true;
-                for (int64_t j = it0; j < njobs && ok; j += istride) {
-                    int64_t it;
-                    int nt0, nt1;
-                    job_of(P, nit, j, it, nt0, nt1);
-                    for (int nt = nt0; nt < nt1 && ok; ++nt)
-                        for (int kb = 0; kb < P.kblocks; ++kb) {
-                            if (!wait_bounded(smem_u32(&S.full[s]), ph, S.abort_flag, P.err, P.timeout_ns)) {
-                                ok = false;
-                                break;
-                            }
-                            mbar_arrive_cluster(mapa_shared(smem_u32(&S.conv[s]), 0u));
-                            if (++s == P.stages) { s = 0; ph ^= 1; }
-                        }
-                }
-                if (!ok) stop_peer();
-                // the even CTA's last commit: all MMAs that touch this CTA are complete
-                else if (!wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns))
-                    stop_peer();
-            }
+            // the even CTA's last commit: all MMAs that touch this CTA are complete
+            if (lane == 0 && !wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns)) stop_peer();
         } else if (lane == 0) {
             // -------------------------------------------------------- MMA issuer
             const bool bf = P.mode != MODE_FP16X3;
@@ -555,9 +550,10 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                         const int kb0 = g * P.group, kb1 = min(P.kblocks, kb0 + P.group);
                         for (int kb = kb0; kb < kb1; ++kb) {
                             const uint64_t *ready = ROT ? &S.conv[s] : &S.full[s];
-                            if (!wait_bounded(smem_u32(ready), ph, S.abort_flag, P.err, P.timeout_ns) ||
-                                (PAIR && !wait_bounded_cluster(smem_u32(&S.conv[s]), ph, S.abort_flag, P.err,
-                                                               P.timeout_ns))) {
+                            const bool in = PAIR ? wait_bounded_cluster(smem_u32(ready), ph, S.abort_flag, P.err,
+                                                                        P.timeout_ns)
+                                                 : wait_bounded(smem_u32(ready), ph, S.abort_flag, P.err, P.timeout_ns);
+                            if (!in) {
                                 ok = false;
                                 break;
                             }
@@ -1017,13 +1013,15 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         return (v && v[0] == '1') ? 1 : 0;
     }();
     P.prefetch = prefetch;
-    // the two-CTA contraction serves every full-grid call; RMS_GEMM_PAIR=0 selects the
-    // single-CTA kernel instead (a measurement switch: both compute the same sums)
-    static const bool pair_ok = [] {
+    // the two-CTA contraction serves full-grid calls unless the plan asks for single
+    // CTAs (rms_plan_set_option); RMS_GEMM_PAIR=0 in the environment makes single CTAs
+    // the default
+    static const bool pair_default = [] {
         const char *v = std::getenv("RMS_GEMM_PAIR");
         return !(v && v[0] == '0');
     }();
-    const bool pair = !rot && pair_ok && p.pair_maps;
+    const bool pair_wanted = p.contraction == RMS_CONTRACT_PAIR || (p.contraction == RMS_CONTRACT_AUTO && pair_default);
+    const bool pair = !rot && pair_wanted && p.pair_maps;
     P.b_rows = pair ? p.tile_n / 2 : p.tile_n;
     P.stages = gemm_stages(P.b_rows, mode);
     if (P.stages < 2) return cudaErrorInvalidConfiguration;
@@ -1065,13 +1063,14 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     // all M tiles in flight plus the whole phase matrix fit there.  Otherwise split:
     // single-N-tile jobs in panels (see GemmParams), with the smallest number of
     // panels whose working set -- the operands of the M tiles the CTAs share at one
-    // time plus one panel of the phase matrix -- fits the budget.  RMS_L2_BUDGET_MB
-    // (8 .. 1024) overrides the 80 MB budget (a tuning knob).
-    static const double budget = [] {
+    // time plus one panel of the phase matrix -- fits the budget (80 MiB by default;
+    // rms_plan_set_option, or RMS_L2_BUDGET_MB = 8 .. 1024 in the environment).
+    static const double budget_default = [] {
         const char *v = std::getenv("RMS_L2_BUDGET_MB");
         const int mb = v ? std::atoi(v) : 0;
         return (mb >= 8 && mb <= 1024 ? mb : 80) * 1048576.0;
     }();
+    const double budget = p.l2_budget > 0 ? (double)p.l2_budget : budget_default;
     P.jobs_split = 0;
     P.npanels = 1;
     P.keys = nullptr;
@@ -1105,11 +1104,26 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         auto kern = gemm_kernel<kHalfRot, true, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<units, 512, smem, s>>>(P, bhi, blo);
+        kern<<<units, 512, smem, s>>>(P, bhi, blo, bhi);   // (the last map is unused here)
     } else if (pair) {
         if (p.tile_n > 2 * kHalf || (p.tile_n & 15) || (p.tile_n_last & 15)) return cudaErrorInvalidValue;
         const CUtensorMap &bhi = chan ? p.tmap2_bhi : p.tmap2_bhi_raw, &blo = chan ? p.tmap2_blo : p.tmap2_blo_raw;
         const int pairs = units;
+        // the operand image as a 3-D tensor for the pair's TMA loads: 64-byte rows, 256
+        // rows (hi then lo parts) per 16 KB block, one block per (M tile, K block); a
+        // stage is one block's first a_rows rows
+        CUtensorMap tmA;
+        {
+            const int64_t nblocks = (((int64_t)o.nlos + 2 * kTileM - 1) / (2 * kTileM)) * 2 * P.kblocks;
+            const cuuint64_t dims[3] = {(cuuint64_t)kKBlock, (cuuint64_t)(2 * kTileM), (cuuint64_t)nblocks};
+            const cuuint64_t strides[2] = {(cuuint64_t)kRowBytes, (cuuint64_t)(2 * kStageA)};
+            const cuuint32_t box[3] = {(cuuint32_t)kKBlock, (cuuint32_t)(split_mode(mode) ? 2 * kTileM : kTileM), 1};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            if (nblocks > 0x7fffffff ||
+                !encode_tensor_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT16, const_cast<uint8_t *>(o.A), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_SWIZZLE_NONE, 3))
+                return cudaErrorInvalidValue;
+        }
         auto kern = gemm_kernel<kHalf, false, true>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1125,7 +1139,7 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, P, bhi, blo);
+        e = cudaLaunchKernelEx(&cfg, kern, P, bhi, blo, tmA);
         if (e != cudaSuccess) return e;
     } else {
         if (p.tile_n > 2 * kHalf) return cudaErrorInvalidValue;
@@ -1133,7 +1147,7 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         auto kern = gemm_kernel<kHalf, false, false>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<units, kThreads, smem, s>>>(P, bhi, blo);
+        kern<<<units, kThreads, smem, s>>>(P, bhi, blo, bhi);   // (the last map is unused here)
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     p.last_ctas = pair ? 2 * units : units;

@@ -85,6 +85,9 @@ struct rms_plan_s {
     // the contraction, 1 if it ran as CTA pairs, N panels of the split schedule (0:
     // whole schedule), kernels launched by the call
     mutable int32_t last_ctas = 0, last_pair = 0, last_panels = 0, last_kernels = 0;
+    // scheduling options (rms_plan_set_option): RMS_CONTRACT_*, L2 budget in bytes (0: default)
+    int32_t contraction = 0;
+    int64_t l2_budget = 0;
 
     // optional kernel timing (rms_plan_set_kernel_timing): events around the layout
     // stage and the contraction of each tensor-core synthesis call
@@ -207,4 +210,4 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
 // api.cu: cuTensorMapEncodeTiled through the runtime's driver entry point
 bool encode_tensor_map(CUtensorMap *map, CUtensorMapDataType type, void *base, const cuuint64_t *dims,
                        const cuuint64_t *strides, const cuuint32_t *box, const cuuint32_t *estr,
-                       CUtensorMapSwizzle swizzle);
+                       CUtensorMapSwizzle swizzle, int rank = 2);

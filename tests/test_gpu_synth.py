@@ -483,3 +483,62 @@ def test_bounded_wait_gives_up_and_reports(rms, inputs):
         Q, U = inputs.make_cube(cfg)
         F, pidx, pabs, pphi = run(rms, plan, Q, U, "chan", cfg.nlos)              # still synthesises
         assert np.all(pidx >= 0)
+
+
+# ------------------------------------------------------------------- contraction schedules
+@pytest.mark.parametrize("path", ["bf16x3", "fp16x3", "bf16"])
+@pytest.mark.parametrize("layout", ["chan", "los"])
+def test_schedules_agree(rms, inputs, oracle_mod, path, layout):
+    """The contraction's schedules on a 1536-channel x 4001-phi cube (the MWA band),
+    16,384 + 77 LOS (a ragged last tile and an odd number of M tiles): single CTAs
+    and CTA pairs, each with the whole schedule (every CTA runs all phase tiles of
+    its M tile) and the split one (single-tile jobs in phase-matrix panels, peaks
+    merged by atomics).  Within one kernel the two schedules run the same MMAs per
+    tile, so F and the peak outputs are bit-identical; the kernels are compared
+    with each other and sampled rows with the oracle."""
+    cfg = inputs.CONFIGS["mwa"]
+    freq, w, phi = axes(inputs, cfg)
+    nlos = 16384 + 77
+    Q, U = inputs.make_cube(cfg, 0, nlos)
+    dev = torch.device("cuda")
+    from paper_1810_06250_gb300.inputs import to_layout
+    q = torch.from_numpy(to_layout(Q, layout)).to(dev)
+    u = torch.from_numpy(to_layout(U, layout)).to(dev)
+    rows = np.r_[np.arange(0, nlos, 331), nlos - 1]
+    op = oracle_mod.plan(freq, "freq", w)
+    Fo = oracle_mod.synth(Q[rows], U[rows], op, phi)
+    got = {}
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        for kind in (rms.RMS_CONTRACT_SINGLE, rms.RMS_CONTRACT_PAIR):
+            for budget in (1 << 40, 16 << 20):
+                rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_CONTRACTION, kind)
+                rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_L2_BUDGET, budget)
+                F = torch.full((nlos, cfg.nphi, 2), float("nan"), device=dev)
+                pi = torch.full((nlos,), -7, dtype=torch.int32, device=dev)
+                pa, pp, pq, pu, pc = (torch.zeros(nlos, device=dev) for _ in range(5))
+                rms.rms_synth_peaks(plan.handle, q, u, nlos, layout, F, pi, pa, pp, pq, pu, pc)
+                plan.sync()
+                sched = (rms.rms_plan_info(plan.handle, rms.RMS_INFO_LAST_PAIR),
+                         rms.rms_plan_info(plan.handle, rms.RMS_INFO_LAST_PANELS))
+                assert sched[0] == (kind == rms.RMS_CONTRACT_PAIR)
+                assert (sched[1] > 0) == (budget < (1 << 30)), sched
+                got[(kind, budget)] = [t.cpu().numpy() for t in (F, pi, pa, pp, pq, pu, pc)]
+    for kind in (rms.RMS_CONTRACT_SINGLE, rms.RMS_CONTRACT_PAIR):
+        whole, split = got[(kind, 1 << 40)], got[(kind, 16 << 20)]
+        for a, b in zip(whole, split):
+            np.testing.assert_array_equal(a, b)
+    for kind in (rms.RMS_CONTRACT_SINGLE, rms.RMS_CONTRACT_PAIR):
+        F, pi, pa, pp, pq, pu, pc = got[(kind, 16 << 20)]
+        ok, info = gh.gate(path, F[rows, :, 0] + 1j * F[rows, :, 1], Fo)
+        assert ok, info
+        gh.check_peaks_self(F, pi, pa, pp, phi)
+        gh.check_peaks_oracle(pi[rows], Fo, gh.TOL[path])
+        # F at the peak is the stored F there
+        k = pi >= 0
+        np.testing.assert_array_equal(pq[k], F[np.nonzero(k)[0], pi[k], 0])
+        np.testing.assert_array_equal(pu[k], F[np.nonzero(k)[0], pi[k], 1])
+    Fs, Fp = got[(rms.RMS_CONTRACT_SINGLE, 1 << 40)][0], got[(rms.RMS_CONTRACT_PAIR, 1 << 40)][0]
+    d = np.abs((Fs[..., 0] - Fp[..., 0]) + 1j * (Fs[..., 1] - Fp[..., 1])).max(axis=1)
+    m = np.abs(Fs[..., 0] + 1j * Fs[..., 1]).max(axis=1)
+    print("single vs pair: max per-LOS difference %.3g, bit-identical %s" % ((d / m).max(), bool((d == 0).all())))
+    assert (d / m).max() <= 1e-6
