@@ -294,10 +294,12 @@ rms_status rms_plan_set_timeout(rms_plan_t plan, int64_t ns);
 /*
  * How the tensor-core contraction of a plan is scheduled (no paper counterpart;
  * for measurement and tuning -- none of these changes a result):
- *   RMS_OPT_CONTRACTION  RMS_CONTRACT_AUTO (default): CTA pairs when the plan's
- *                        tiles allow them; RMS_CONTRACT_SINGLE: one CTA per 128-row
- *                        MMA; RMS_CONTRACT_PAIR: CTA pairs (256-row MMAs on two SMs,
- *                        each SM holding half of the phase tile), or
+ *   RMS_OPT_CONTRACTION  RMS_CONTRACT_AUTO (default): CTA pairs when the plan's pair
+ *                        tiles are wider than 208 phase rows (2 nphi > 832 or so),
+ *                        single CTAs otherwise; RMS_CONTRACT_SINGLE: one CTA per
+ *                        128-row MMA with tiles of up to 208 phase rows;
+ *                        RMS_CONTRACT_PAIR: CTA pairs (256-row MMAs on two SMs, each
+ *                        SM holding half of a tile of up to 256 phase rows), or
  *                        RMS_ERR_UNSUPPORTED when the tiles do not allow them.
  *   RMS_OPT_L2_BUDGET    bytes of L2 the schedule may count on (0 = the default,
  *                        80 MiB).  While the operands of the line-of-sight tiles in

@@ -301,12 +301,19 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
             int t = std::atoi(v);
             if (t >= 16 && t <= max_tile_cap && t % 16 == 0) max_tile = t;
         }
-        p->ntiles_n = (N + max_tile - 1) / max_tile;
-        int per = (N + p->ntiles_n - 1) / p->ntiles_n;
-        p->tile_n = (per + 15) / 16 * 16;
-        int last = N - (p->ntiles_n - 1) * p->tile_n;
-        p->tile_n_last = (last + 15) / 16 * 16;
-        p->npad = p->ntiles_n * p->tile_n;
+        // balanced tiles of at most max_tile rows, each a multiple of 16 (the last one
+        // rounded up to 16 as well)
+        auto tiling = [N](int cap, int32_t &ntiles, int32_t &tile, int32_t &last) {
+            ntiles = (N + cap - 1) / cap;
+            const int per = (N + ntiles - 1) / ntiles;
+            tile = (per + 15) / 16 * 16;
+            last = (N - (ntiles - 1) * tile + 15) / 16 * 16;
+        };
+        tiling(max_tile, p->ntiles_n, p->tile_n, p->tile_n_last);
+        // CTA pairs take tiles of up to 256 rows (plans for the single-CTA window kernel keep theirs)
+        if (max_tile_cap == kMaxTileN) tiling(kMaxTileNPair, p->ntiles_n2, p->tile_n2, p->tile_n_last2);
+        else { p->ntiles_n2 = p->ntiles_n; p->tile_n2 = p->tile_n; p->tile_n_last2 = p->tile_n_last; }
+        p->npad = std::max(p->ntiles_n * p->tile_n, p->ntiles_n2 * p->tile_n2);
         p->kblocks = (p->nact + kChanPerKBlock - 1) / kChanPerKBlock;
         p->kpad = p->kblocks * kKBlock;
         const bool fp16 = precision == RMS_FP16X3;
@@ -347,8 +354,8 @@ rms_status plan_create_internal(rms_plan_t *out, const double *axis, int32_t nch
         }
         // half-tile boxes for the two-CTA contraction (tile_n a multiple of 16, so a
         // half is whole 8-row swizzle groups)
-        if (p->tile_n % 16 == 0 && p->tile_n_last % 16 == 0) {
-            const int h = p->tile_n / 2;
+        if (p->tile_n2 % 16 == 0 && p->tile_n_last2 % 16 == 0) {
+            const int h = p->tile_n2 / 2;
             p->pair_maps = encode_b_map(&p->tmap2_bhi, p->d_bhi, p->kpad, p->npad, h) &&
                            encode_b_map(&p->tmap2_blo, p->d_blo, p->kpad, p->npad, h) &&
                            encode_b_map(&p->tmap2_bhi_raw, p->d_bhi_raw, p->kpad_raw, p->npad, h) &&

@@ -54,6 +54,9 @@ constexpr int kStageA = kTileM * kRowBytes;       // 8 KB per A part
 constexpr int kTmemCols = 512;
 constexpr int kAccStride = 256;
 constexpr int kHalf = kMaxTileN / 2;              // 104 columns per epilogue thread
+constexpr int kHalfWide = 128;                    // CTA pairs: tiles of up to 256 phase rows
+constexpr int kRegsLaunch = 168, kRegsCtl = 56, kRegsEpi = 224;   // setmaxnreg split of the wide variant
+static_assert(128 * kRegsCtl + 256 * kRegsEpi == kThreads * kRegsLaunch, "register split must fill the launch");
 constexpr int kHalfRot = 64;                      // rotating (window) kernel: tile_n <= 128
 constexpr int kEpiCols = 8;                       // staging chunk: 8 columns x 32 rows per warp
 constexpr int kEpiLd = kEpiCols + 1;
@@ -442,6 +445,12 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
     tc_fence_after();
     const uint32_t tmem_base = *S.tmem_slot;
 
+    // Tiles of up to 256 phase rows (HALF > kHalf): each epilogue thread keeps HALF FP32
+    // sums, so warpgroup 0 (producer, MMA issuer) hands registers to the two epilogue
+    // warpgroups at the top of their branches; the shares add up to the launch's
+    // 384 x 168 registers (checked on the host before the first launch).
+    if (warp < 4) {
+    if constexpr (HALF > kHalf) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
@@ -621,6 +630,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             for (size_t off = (size_t)lane * 4096; off < blk; off += 32 * 4096)
                 prefetch_l2(nxt + off, (uint32_t)min((size_t)4096, blk - off));
         }
+    }
     } else if (ROT && warp >= kConvWarp0) {
         // ------------------------------------------------------------ rotation
         // Thread r owns operand row r: P' = (hi + lo) T[centre][channel] in FP32,
@@ -681,6 +691,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 }
         }
     } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kNumEpiWarps) {
+        if constexpr (HALF > kHalf) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;
         const int h = (warp - kEpiWarp0) >> 2;
@@ -983,9 +994,6 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     int ngroups = (P.kblocks + group_max - 1) / group_max;
     P.group = (P.kblocks + ngroups - 1) / ngroups;
     P.nphi = p.nphi;
-    P.ntiles_n = p.ntiles_n;
-    P.tile_n = p.tile_n;
-    P.tile_n_last = p.tile_n_last;
     P.F = o.F;
     P.pidx = o.pidx;
     P.pabs = o.pabs;
@@ -1020,9 +1028,18 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         const char *v = std::getenv("RMS_GEMM_PAIR");
         return !(v && v[0] == '0');
     }();
-    const bool pair_wanted = p.contraction == RMS_CONTRACT_PAIR || (p.contraction == RMS_CONTRACT_AUTO && pair_default);
+    // Automatic choice: pairs where their tiles exceed 208 phase rows (a 256-row MMA
+    // with N <= 208 takes ~116 cycles against ~104 for the 128-row one, so with
+    // narrower tiles single CTAs keep the tensor pipe busier; measured on the LOFAR
+    // cube, 0.86 against 0.77 ms).
+    const bool pair_wanted = p.contraction == RMS_CONTRACT_PAIR ||
+                             (p.contraction == RMS_CONTRACT_AUTO && pair_default && p.tile_n2 > 2 * kHalf);
     const bool pair = !rot && pair_wanted && p.pair_maps;
-    P.b_rows = pair ? p.tile_n / 2 : p.tile_n;
+    P.ntiles_n = pair ? p.ntiles_n2 : p.ntiles_n;
+    P.tile_n = pair ? p.tile_n2 : p.tile_n;
+    P.tile_n_last = pair ? p.tile_n_last2 : p.tile_n_last;
+    const bool wide = pair && P.tile_n > 2 * kHalf;   // the pair kernel with 128 columns per epilogue thread
+    P.b_rows = pair ? P.tile_n / 2 : P.tile_n;
     P.stages = gemm_stages(P.b_rows, mode);
     if (P.stages < 2) return cudaErrorInvalidConfiguration;
     size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(P.b_rows, mode) + 24 * (size_t)P.stages;
@@ -1033,12 +1050,25 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     }
     const int64_t nit = pair ? (nmt + 1) / 2 : nmt;
     int maxunits = pair ? (ctas / 2 > 0 ? ctas / 2 : 1) : ctas;
+    using KernelFn = void (*)(GemmParams, CUtensorMap, CUtensorMap, CUtensorMap);
+    const KernelFn pair_kern = wide ? gemm_kernel<kHalfWide, false, true> : gemm_kernel<kHalf, false, true>;
+    if (wide) {
+        // the wide variant's setmaxnreg shares add up to 384 x 168 registers: launching it
+        // with any other register count would leave its epilogue warpgroups waiting for
+        // registers, so check the build once
+        static const cudaError_t regs_ok = [] {
+            cudaFuncAttributes fa;
+            cudaError_t e1 = cudaFuncGetAttributes(&fa, gemm_kernel<kHalfWide, false, true>);
+            if (e1 != cudaSuccess) return e1;
+            return fa.numRegs == kRegsLaunch ? cudaSuccess : cudaErrorInvalidConfiguration;
+        }();
+        if (regs_ok != cudaSuccess) return regs_ok;
+    }
     if (pair) {
         // a pair needs two SMs of one TPC; TPCs with a disabled SM cannot host one, so
         // the persistent grid takes as many clusters as can be resident at once (more
         // would wait for a second wave)
-        cudaError_t e0 = cudaFuncSetAttribute(gemm_kernel<kHalf, false, true>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e0 = cudaFuncSetAttribute(pair_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e0 != cudaSuccess) return e0;
         cudaLaunchConfig_t qc = {};
         qc.gridDim = dim3((unsigned)(2 * maxunits), 1, 1);
@@ -1052,7 +1082,7 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         qc.attrs = qa;
         qc.numAttrs = 1;
         int nclusters = 0;
-        e0 = cudaOccupancyMaxActiveClusters(&nclusters, gemm_kernel<kHalf, false, true>, &qc);
+        e0 = cudaOccupancyMaxActiveClusters(&nclusters, pair_kern, &qc);
         if (e0 != cudaSuccess) return e0;
         if (nclusters < 1) return cudaErrorInvalidConfiguration;
         if (nclusters < maxunits) maxunits = nclusters;
@@ -1083,8 +1113,8 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         if (whole > budget) {
             int best = 1;
             double best_live = 1e300;
-            for (int np = 1; np <= p.ntiles_n; ++np) {
-                const int len = p.ntiles_n / np;
+            for (int np = 1; np <= P.ntiles_n; ++np) {
+                const int len = P.ntiles_n / np;
                 const double live = ((units + len - 1) / len + 1) * tiles_per_unit * a_tile + b_all / np;
                 if (live <= budget) { best = np; best_live = live; break; }
                 if (live < best_live) { best = np; best_live = live; }
@@ -1106,7 +1136,7 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         if (e != cudaSuccess) return e;
         kern<<<units, 512, smem, s>>>(P, bhi, blo, bhi);   // (the last map is unused here)
     } else if (pair) {
-        if (p.tile_n > 2 * kHalf || (p.tile_n & 15) || (p.tile_n_last & 15)) return cudaErrorInvalidValue;
+        if (P.tile_n > 2 * kHalfWide || (P.tile_n & 15) || (P.tile_n_last & 15)) return cudaErrorInvalidValue;
         const CUtensorMap &bhi = chan ? p.tmap2_bhi : p.tmap2_bhi_raw, &blo = chan ? p.tmap2_blo : p.tmap2_blo_raw;
         const int pairs = units;
         // the operand image as a 3-D tensor for the pair's TMA loads: 64-byte rows, 256
@@ -1124,9 +1154,6 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
                                    box, estr, CU_TENSOR_MAP_SWIZZLE_NONE, 3))
                 return cudaErrorInvalidValue;
         }
-        auto kern = gemm_kernel<kHalf, false, true>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
         cfg.blockDim = dim3(kThreads, 1, 1);
@@ -1139,7 +1166,7 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, P, bhi, blo, tmA);
+        e = cudaLaunchKernelEx(&cfg, pair_kern, P, bhi, blo, tmA);
         if (e != cudaSuccess) return e;
     } else {
         if (p.tile_n > 2 * kHalf) return cudaErrorInvalidValue;

@@ -18,6 +18,7 @@ constexpr int kChanPerKBlock = 16; // active channels per pipeline stage
 constexpr int kKBlock = 32;        // K values (Q and U interleaved) per stage = 64 bytes of bf16
 constexpr int kMaxTileN = 208;     // phase-matrix rows per tile: each of the two epilogue warps
                                    // sharing a row keeps tile_n / 2 FP32 sums in registers
+constexpr int kMaxTileNPair = 256; // CTA pairs: the largest N of a 256-row MMA
 constexpr int kGroupKBlocks = 8;   // K blocks accumulated in TMEM before the FP32 register fold (split precisions)
 
 struct rms_plan_s {
@@ -42,6 +43,8 @@ struct rms_plan_s {
     float2 *d_czt = nullptr;       // chirp-z constants: H [M], twiddles [2 M], g [nchan], v [nphi]
     int32_t czt_M = 0;             // chirp-z FFT length
     int32_t kpad = 0, npad = 0, tile_n = 0, ntiles_n = 0, tile_n_last = 0, kblocks = 0;
+    // the tiling of the two-CTA contraction: up to 256 phase rows per tile (npad covers both)
+    int32_t tile_n2 = 0, ntiles_n2 = 0, tile_n_last2 = 0;
     CUtensorMap tmap_bhi;   // CUtensorMap is 64-byte aligned by its own declaration
     CUtensorMap tmap_blo;
     // LOS-major cubes contract over all channels (flagged ones zeroed in the
