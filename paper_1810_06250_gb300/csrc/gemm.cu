@@ -29,7 +29,7 @@
 // once both halves are in.  Commits go to the barriers of both CTAs (multicast),
 // and the epilogue warps of both CTAs release a TMEM partial on the even CTA's
 // barrier.
-// MMAs run in groups of a few K blocks into one of two TMEM partials and the
+// MMAs run in groups of up to 16 K blocks into one of two TMEM partials and the
 // epilogue folds each partial into FP32 registers with round-to-nearest adds,
 // because the tensor core's own FP32 accumulation does not round to nearest.
 // Every wait is bounded: a wait that runs out aborts the CTA, records
@@ -984,11 +984,11 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     // K blocks chained into one TMEM partial before the round-to-nearest fold: the
     // tensor core's accumulation error grows ~4e-8 per chained MMA, which matters for
     // the split precisions only; plain BF16 (error ~1e-3) folds once per N tile.
-    // RMS_GROUP_KBLOCKS (2..16) overrides the split-precision group (a tuning knob).
+    // RMS_GROUP_KBLOCKS (2..64) overrides the split-precision group (a tuning knob).
     static const int group_split = [] {
         const char *v = std::getenv("RMS_GROUP_KBLOCKS");
         const int g = v ? std::atoi(v) : 0;
-        return (g >= 2 && g <= 16) ? g : kGroupKBlocks;
+        return (g >= 2 && g <= 64) ? g : kGroupKBlocks;
     }();
     const int group_max = mode == MODE_BF16 ? P.kblocks : group_split;
     int ngroups = (P.kblocks + group_max - 1) / group_max;

@@ -35,7 +35,7 @@ def test_committed_profiles_record_hash_and_traffic():
     # every summary bench.py reads traffic from names the source hash it was taken on
     # and the bytes per launch (bench.py reports null once the source has changed)
     import re
-    for name in ("gemm_lofar_bf16x3.md", "czt_lofar_ul2.md"):
+    for name in ("gemm_mwa_bf16x3.md", "gemm_lofar_bf16x3.md", "czt_lofar_ul2.md"):
         text = open(os.path.join(ROOT, "profiles", name)).read()
         assert re.search(r"sha256\[:16\] [0-9a-f]{16}", text), name
         assert re.search(r"traffic_bytes_per_launch: \d+", text), name
