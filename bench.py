@@ -604,8 +604,8 @@ def measure_learned(args, dev, local, rank, world, barrier, steps, warmup):
     import torch
     import paper_1810_06250_gb300 as rms
     from paper_1810_06250_gb300 import inputs, learned as Lm
-    path = path if args.config == "learned" else "bf16x3"
-    layout = layout if args.config == "learned" else "chan"
+    path = args.path if args.config == "learned" else "bf16x3"
+    layout = args.layout if args.config == "learned" else "chan"
     cfg = inputs.CONFIGS["learned"]
     if args.nlos is not None:
         import dataclasses
