@@ -24,6 +24,19 @@
  *    by rms_plan_sync and by the next rms_synth on that plan.
  *  - Nothing in the library calls exit(), abort() or a device trap.
  *  - Units: lambda^2 in m^2, frequency in Hz, phi in rad m^-2.
+ *  - Tuning knobs: environment variables read once per process, for measurement.
+ *    None of them changes what is computed beyond FP32 rounding order, and unset
+ *    (or out-of-range) means the documented default:
+ *      RMS_MAX_TILE_N (16..208)    phase rows per single-CTA tile (plan creation);
+ *      RMS_GEMM_PAIR=0             single CTAs instead of CTA pairs by default;
+ *      RMS_L2_BUDGET_MB (8..1024)  L2 budget of the contraction's schedule (80);
+ *      RMS_GROUP_KBLOCKS (2..64)   K blocks per TMEM partial before the FP32 fold of
+ *                                  the split precisions (16; more chained MMAs add
+ *                                  accumulation error: per LOS on the 1536-channel
+ *                                  MWA cube, BF16X3 4.6e-6 at 16 and 6.1e-6 at 32);
+ *      RMS_GEMM_CTAS (1..SMs)      persistent CTAs of the contraction;
+ *      RMS_L2_PREFETCH=1           L2 prefetch of the next M tile (single CTAs, whole schedule);
+ *      RMS_HOST_CHUNK (>= 1024)    LOS per chunk of rms_synth_host.
  *  - A plan may be used from several streams.  The tensor-core precisions keep
  *    a per-plan scratch for split operands, so every synthesis call on a plan
  *    waits on the device for the previous call on that plan (an event recorded

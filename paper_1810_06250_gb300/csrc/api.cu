@@ -564,9 +564,11 @@ rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t 
     // (the caller's stream), copy out (stream d2h), so the three overlap.  A cube of
     // fewer than two chunks runs as one chunk.
     constexpr int kSlots = 3;
-    // Chunk sizes measured on GB300 (LOFAR cube, pinned memory): LOS-major chunks are
-    // contiguous, and 16 of them pipeline best; a channel-major chunk is a 2-D copy of
-    // one row per channel, efficient only when rows are >= 256 KB (65536 LOS).
+    // Chunk sizes measured on GB300 (pinned memory): LOS-major chunks are contiguous, and
+    // 16 of them pipeline best (LOFAR cube); a channel-major chunk is a 2-D copy of one
+    // row per channel, efficient only when rows are >= 256 KB (65536 LOS), and at least 8
+    // chunks keep the pipeline's fill and drain short (MWA cube, 1M LOS: 205 ms per call
+    // with 8 chunks, 260 ms with 4; the 33.6 GB of F leaving over the host link set ~196 ms).
     // RMS_HOST_CHUNK (LOS, >= 1024) overrides the chunk size (a tuning knob).
     static const int64_t knob = [] {
         const char *v = std::getenv("RMS_HOST_CHUNK");
@@ -575,7 +577,7 @@ rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t 
     }();
     const int64_t chunk = knob ? knob
                                : layout == RMS_LOS_MAJOR ? std::max<int64_t>(16384, (nlos + 15) / 16)
-                                                         : std::max<int64_t>(65536, (nlos + 3) / 4);
+                                                         : std::max<int64_t>(65536, (nlos + 7) / 8);
     const int64_t nchunks = (nlos + chunk - 1) / chunk;
     const int slots = (int)std::min<int64_t>(kSlots, nchunks);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };

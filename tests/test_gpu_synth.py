@@ -542,3 +542,41 @@ def test_schedules_agree(rms, inputs, oracle_mod, path, layout):
     m = np.abs(Fs[..., 0] + 1j * Fs[..., 1]).max(axis=1)
     print("single vs pair: max per-LOS difference %.3g, bit-identical %s" % ((d / m).max(), bool((d == 0).all())))
     assert (d / m).max() <= 1e-6
+
+
+@pytest.mark.parametrize("nlos", [1, 127, 128, 129, 256, 383])
+def test_pair_edges(rms, inputs, oracle_mod, nlos):
+    """CTA pairs on small and ragged cubes: 1536 channels (the MWA band) x 801 phi, whose
+    phase rows tile as 7 x 240 (> 208, so pairs are chosen), with 1 to 3 M tiles (an
+    odd count leaves the last pair's odd CTA a padding tile); both schedules, F and the
+    peak outputs against the oracle, and Q, U, chi0 at the peak with and without a
+    stored F (without F the whole schedule is kept)."""
+    cfg = inputs.CONFIGS["mwa"]
+    freq, w = inputs.frequencies(cfg), inputs.weights(cfg)
+    phi = np.linspace(-400.0, 400.0, 801)
+    Q, U = inputs.make_cube(cfg, 777, nlos)
+    op = oracle_mod.plan(freq, "freq", w)
+    Fo = oracle_mod.synth(Q, U, op, phi)
+    dev = torch.device("cuda")
+    q = torch.from_numpy(inputs.to_layout(Q, "chan")).to(dev)
+    u = torch.from_numpy(inputs.to_layout(U, "chan")).to(dev)
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        outs = []
+        for budget, with_f in ((1 << 40, True), (1 << 20, True), (1 << 20, False)):
+            rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_L2_BUDGET, budget)
+            F = torch.full((nlos, len(phi), 2), float("nan"), device=dev) if with_f else None
+            pi = torch.full((nlos,), -7, dtype=torch.int32, device=dev)
+            pa, pp, pq, pu, pc = (torch.zeros(nlos, device=dev) for _ in range(5))
+            rms.rms_synth_peaks(plan.handle, q, u, nlos, "chan", F, pi, pa, pp, pq, pu, pc)
+            plan.sync()
+            assert rms.rms_plan_info(plan.handle, rms.RMS_INFO_LAST_PAIR) == 1
+            outs.append([None if F is None else F.cpu().numpy()] + [t.cpu().numpy() for t in (pi, pa, pp, pq, pu, pc)])
+        F = outs[0][0]
+        ok, info = gh.gate("bf16x3", F[..., 0] + 1j * F[..., 1], Fo)
+        assert ok, info
+        gh.check_peaks_self(F, *outs[0][1:4], phi)
+        gh.check_peaks_oracle(outs[0][1], Fo, gh.TOL["bf16x3"])
+        for o in outs[1:]:                # the other schedules: identical peak outputs
+            for a, b in zip(outs[0][1:], o[1:]):
+                np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(outs[0][0], outs[1][0])
