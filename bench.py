@@ -184,21 +184,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def measured_traffic(kernel_src: str, summary: str):
-    """DRAM bytes per launch from a committed ncu summary, or None when the kernel
-    source has changed since the counters were taken (sha256 prefix recorded there)."""
+def profile_value(kernel_src: str, summary: str, key: str):
+    """A `key: value` line of a committed ncu summary, or None when the kernel source
+    has changed since the counters were taken (sha256 prefix recorded there)."""
     import hashlib
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        m = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+        m = re.search(r"%s: ([0-9.]+)" % re.escape(key), text)
         h = re.search(r"sha256\[:16\] ([0-9a-f]{16})", text)
         src = open(os.path.join(ROOT, "paper_1810_06250_gb300", "csrc", kernel_src), "rb").read()
         if m and h and hashlib.sha256(src).hexdigest()[:16] == h.group(1):
-            return int(m.group(1))
+            return float(m.group(1))
     except OSError:
         pass
     return None
+
+
+def measured_traffic(kernel_src: str, summary: str):
+    """DRAM bytes per launch from a committed ncu summary (None when the source changed)."""
+    v = profile_value(kernel_src, summary, "traffic_bytes_per_launch")
+    return None if v is None else int(v)
 
 
 def workload_name(cfg, nact, layout, peak_only=False):
@@ -370,6 +376,14 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
         traffic = measured_traffic("gemm.cu", "gemm_%s_bf16x3.md" % cfg_name) \
             if (path == "bf16x3" and layout == "chan" and full_size) else None
         roof = tensor_roofline(path, useful_flops, kt, total_ms * 1e-3, peaks, traffic, avg_launch_ms, hbm_bytes)
+        if traffic is not None:
+            # the ncu counters of the same capture (a smaller case of this workload, same kernel source)
+            roof["ncu"] = {"summary": "profiles/gemm_%s_bf16x3.md" % cfg_name,
+                           "tensor_pipe_active_pct": profile_value("gemm.cu", "gemm_%s_bf16x3.md" % cfg_name,
+                                                                   "tensor_pipe_active_pct"),
+                           "dram_throughput_pct": profile_value("gemm.cu", "gemm_%s_bf16x3.md" % cfg_name,
+                                                                "dram_throughput_pct"),
+                           "hbm_gbs_full_size": traffic / (roof["launch_ms"] * 1e-3) / 1e9}
         roof["schedule"] = dict(sched, note="n_panels 0: each CTA runs every phase tile of its M tile; k > 0: "
                                             "single-tile jobs in k panels of the phase matrix, peaks merged by "
                                             "64-bit atomics and a finalize kernel")

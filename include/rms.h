@@ -28,7 +28,7 @@
  *    None of them changes what is computed beyond FP32 rounding order, and unset
  *    (or out-of-range) means the documented default:
  *      RMS_MAX_TILE_N (16..208)    phase rows per single-CTA tile (plan creation);
- *      RMS_GEMM_PAIR=0             single CTAs instead of CTA pairs by default;
+ *      RMS_GEMM_PAIR=0 | 2         single CTAs by default | pairs wherever tiles allow;
  *      RMS_L2_BUDGET_MB (8..1024)  L2 budget of the contraction's schedule (80);
  *      RMS_GROUP_KBLOCKS (2..64)   K blocks per TMEM partial before the FP32 fold of
  *                                  the split precisions (16; more chained MMAs add
@@ -314,17 +314,23 @@ rms_status rms_plan_set_timeout(rms_plan_t plan, int64_t ns);
  *                        RMS_CONTRACT_PAIR: CTA pairs (256-row MMAs on two SMs, each
  *                        SM holding half of a tile of up to 256 phase rows), or
  *                        RMS_ERR_UNSUPPORTED when the tiles do not allow them.
- *   RMS_OPT_L2_BUDGET    bytes of L2 the schedule may count on (0 = the default,
- *                        80 MiB).  While the operands of the line-of-sight tiles in
- *                        flight plus the whole phase matrix fit, every CTA runs all
- *                        phase tiles of its lines of sight; otherwise it runs
- *                        single-tile jobs in panels of the phase matrix and the peak
- *                        map is merged afterwards.  Both give bit-identical outputs.
- * The environment variables RMS_GEMM_PAIR=0 and RMS_L2_BUDGET_MB=<MiB>, read once
- * per process, change the defaults of new plans.  Synchronous; RMS_ERR_INVALID_ARG
+ *   RMS_OPT_SCHEDULE     RMS_SCHEDULE_AUTO (default): single-tile jobs (one line-of-
+ *                        sight tile against one phase tile), dealt round-robin in
+ *                        panels of the phase matrix, the peak map merged afterwards --
+ *                        except for rms_synth_peaks calls that want Q, U or chi0 at the
+ *                        peak without F_out; RMS_SCHEDULE_WHOLE: every CTA runs all
+ *                        phase tiles of its lines of sight.  Both give bit-identical
+ *                        outputs.
+ *   RMS_OPT_L2_BUDGET    bytes of L2 the job schedule may count on (0 = the default,
+ *                        80 MiB): the fewest panels whose working set (the operands
+ *                        of the line-of-sight tiles in flight plus one panel of the
+ *                        phase matrix) fits.
+ * The environment variables RMS_GEMM_PAIR=0 (or 2: pairs wherever the tiles allow)
+ * and RMS_L2_BUDGET_MB=<MiB>, read once per process, change the defaults.  Synchronous; RMS_ERR_INVALID_ARG
  * for an unknown option or value.
  */
-enum { RMS_OPT_CONTRACTION = 0, RMS_OPT_L2_BUDGET = 1 };
+enum { RMS_OPT_CONTRACTION = 0, RMS_OPT_L2_BUDGET = 1, RMS_OPT_SCHEDULE = 2 };
+enum { RMS_SCHEDULE_AUTO = 0, RMS_SCHEDULE_WHOLE = 1 };
 enum { RMS_CONTRACT_AUTO = 0, RMS_CONTRACT_SINGLE = 1, RMS_CONTRACT_PAIR = 2 };
 rms_status rms_plan_set_option(rms_plan_t plan, int32_t option, int64_t value);
 

@@ -24,7 +24,8 @@ from ._binding import (  # noqa: F401
     rms_propose, rms_net_grad, rms_train_step, rms_window_create, rms_window_destroy, rms_synth_window,
     rms_peakmap_learned, rms_plan_set_kernel_timing, rms_plan_kernel_times, rms_peak_outputs, rms_synth_peaks,
     rms_selftest_wait_timeout, rms_clean_create, rms_clean_destroy, rms_clean, rms_refine_peaks,
-    rms_window_centres, rms_plan_set_option, RMS_OPT_CONTRACTION, RMS_OPT_L2_BUDGET, RMS_CONTRACT_AUTO,
+    rms_window_centres, rms_plan_set_option, RMS_OPT_CONTRACTION, RMS_OPT_L2_BUDGET, RMS_OPT_SCHEDULE, RMS_SCHEDULE_AUTO,
+    RMS_SCHEDULE_WHOLE, RMS_CONTRACT_AUTO,
     RMS_CONTRACT_SINGLE, RMS_CONTRACT_PAIR,
 )
 

@@ -248,7 +248,8 @@ def rms_plan_sync(plan: int, stream=None):
     _check(load().rms_plan_sync(plan, _stream(stream)), "rms_plan_sync")
 
 
-RMS_OPT_CONTRACTION, RMS_OPT_L2_BUDGET = 0, 1
+RMS_OPT_CONTRACTION, RMS_OPT_L2_BUDGET, RMS_OPT_SCHEDULE = 0, 1, 2
+RMS_SCHEDULE_AUTO, RMS_SCHEDULE_WHOLE = 0, 1
 RMS_CONTRACT_AUTO, RMS_CONTRACT_SINGLE, RMS_CONTRACT_PAIR = 0, 1, 2
 
 

@@ -725,6 +725,10 @@ rms_status rms_plan_set_option(rms_plan_t p, int32_t option, int64_t value)
         if (value < 0) return RMS_ERR_INVALID_ARG;
         p->l2_budget = value;
         return RMS_OK;
+    case RMS_OPT_SCHEDULE:
+        if (value < RMS_SCHEDULE_AUTO || value > RMS_SCHEDULE_WHOLE) return RMS_ERR_INVALID_ARG;
+        p->schedule = (int32_t)value;
+        return RMS_OK;
     default: return RMS_ERR_INVALID_ARG;
     }
 }

@@ -1022,18 +1022,24 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     }();
     P.prefetch = prefetch;
     // the two-CTA contraction serves full-grid calls unless the plan asks for single
-    // CTAs (rms_plan_set_option); RMS_GEMM_PAIR=0 in the environment makes single CTAs
-    // the default
-    static const bool pair_default = [] {
+    // CTAs (rms_plan_set_option); in the environment RMS_GEMM_PAIR=0 makes single CTAs
+    // the default and RMS_GEMM_PAIR=2 CTA pairs wherever the tiles allow them
+    static const int pair_default = [] {
         const char *v = std::getenv("RMS_GEMM_PAIR");
-        return !(v && v[0] == '0');
+        return v && v[0] == '0' ? 0 : (v && v[0] == '2' ? 2 : 1);
     }();
-    // Automatic choice: pairs where their tiles exceed 208 phase rows (a 256-row MMA
-    // with N <= 208 takes ~116 cycles against ~104 for the 128-row one, so with
-    // narrower tiles single CTAs keep the tensor pipe busier; measured on the LOFAR
-    // cube, 0.86 against 0.77 ms).
-    const bool pair_wanted = p.contraction == RMS_CONTRACT_PAIR ||
-                             (p.contraction == RMS_CONTRACT_AUTO && pair_default && p.tile_n2 > 2 * kHalf);
+    // Automatic choice: pairs where their tiles exceed 208 phase rows; with narrower
+    // tiles (a 256-row MMA with N <= 208 takes ~116 cycles against ~104 for the 128-row
+    // one) only for split precisions under the job schedule, where the halved
+    // shared-memory traffic wins (LOFAR cube, BF16x3: 0.68 against 0.70 ms
+    // channel-major, 0.69 against 0.74 LOS-major; whole schedule 0.87 against 0.75;
+    // plain BF16 0.53 against 0.50).
+    const bool f_at_peak = o.pq || o.pu || o.pchi;
+    const bool jobs = !rot && o.keys && p.schedule != RMS_SCHEDULE_WHOLE && (o.F || !f_at_peak);
+    const bool pair_wanted =
+        p.contraction == RMS_CONTRACT_PAIR ||
+        (p.contraction == RMS_CONTRACT_AUTO &&
+         (pair_default == 2 || (pair_default == 1 && (p.tile_n2 > 2 * kHalf || (jobs && split_mode(mode))))));
     const bool pair = !rot && pair_wanted && p.pair_maps;
     P.ntiles_n = pair ? p.ntiles_n2 : p.ntiles_n;
     P.tile_n = pair ? p.tile_n2 : p.tile_n;
@@ -1090,11 +1096,12 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     const int units = (int)(nit < maxunits ? nit : maxunits);
     // Schedule.  Whole: every CTA (pair) runs all N tiles of its M tile(s), re-reading
     // their operand once per N tile; those re-reads hit L2 only while the operands of
-    // all M tiles in flight plus the whole phase matrix fit there.  Otherwise split:
-    // single-N-tile jobs in panels (see GemmParams), with the smallest number of
-    // panels whose working set -- the operands of the M tiles the CTAs share at one
-    // time plus one panel of the phase matrix -- fits the budget (80 MiB by default;
-    // rms_plan_set_option, or RMS_L2_BUDGET_MB = 8 .. 1024 in the environment).
+    // all M tiles in flight plus the whole phase matrix fit there.  Split (the default
+    // when the caller provides key scratch): single-N-tile jobs in panels (see
+    // GemmParams), with the smallest number of panels whose working set -- the
+    // operands of the M tiles the CTAs share at one time plus one panel of the phase
+    // matrix -- fits the budget (80 MiB by default; rms_plan_set_option, or
+    // RMS_L2_BUDGET_MB = 8 .. 1024 in the environment).
     static const double budget_default = [] {
         const char *v = std::getenv("RMS_L2_BUDGET_MB");
         const int mb = v ? std::atoi(v) : 0;
@@ -1104,13 +1111,14 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.jobs_split = 0;
     P.npanels = 1;
     P.keys = nullptr;
-    const bool f_at_peak = o.pq || o.pu || o.pchi;
-    if (!rot && o.keys && (o.F || !f_at_peak)) {
+    if (jobs) {
         const double tiles_per_unit = pair ? 2.0 : 1.0;
         const double a_tile = (double)P.kblocks * (split_mode(mode) ? 2 * kStageA : kStageA);
         const double b_all = (double)p.npad * (chan ? p.kpad : p.kpad_raw) * 2.0 * (split_mode(mode) ? 2 : 1);
-        const double whole = units * tiles_per_unit * a_tile + b_all;
-        if (whole > budget) {
+        // measured on the LOFAR cube: split jobs 0.70 ms against 0.75 ms for the whole
+        // schedule although the latter's working set fits (finer jobs balance the CTAs
+        // better), so the split schedule is the default wherever the call has the keys
+        {
             int best = 1;
             double best_live = 1e300;
             for (int np = 1; np <= P.ntiles_n; ++np) {

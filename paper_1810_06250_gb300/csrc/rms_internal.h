@@ -91,7 +91,7 @@ struct rms_plan_s {
     // whole schedule), kernels launched by the call
     mutable int32_t last_ctas = 0, last_pair = 0, last_panels = 0, last_kernels = 0;
     // scheduling options (rms_plan_set_option): RMS_CONTRACT_*, L2 budget in bytes (0: default)
-    int32_t contraction = 0;
+    int32_t contraction = 0, schedule = 0;
     int64_t l2_budget = 0;
 
     // optional kernel timing (rms_plan_set_kernel_timing): events around the layout

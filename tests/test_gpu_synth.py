@@ -492,8 +492,8 @@ def test_schedules_agree(rms, inputs, oracle_mod, path, layout):
     """The contraction's schedules on a 1536-channel x 4001-phi cube (the MWA band),
     16,384 + 77 LOS (a ragged last tile and an odd number of M tiles): single CTAs
     and CTA pairs, each with the whole schedule (every CTA runs all phase tiles of
-    its M tile) and the split one (single-tile jobs in phase-matrix panels, peaks
-    merged by atomics).  Within one kernel the two schedules run the same MMAs per
+    its M tile) and the split one (single-tile jobs in several phase-matrix panels,
+    peaks merged by atomics).  Within one kernel the two schedules run the same MMAs per
     tile, so F and the peak outputs are bit-identical; the kernels are compared
     with each other and sampled rows with the oracle."""
     cfg = inputs.CONFIGS["mwa"]
@@ -512,6 +512,8 @@ def test_schedules_agree(rms, inputs, oracle_mod, path, layout):
         for kind in (rms.RMS_CONTRACT_SINGLE, rms.RMS_CONTRACT_PAIR):
             for budget in (1 << 40, 16 << 20):
                 rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_CONTRACTION, kind)
+                rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_SCHEDULE,
+                                        rms.RMS_SCHEDULE_WHOLE if budget > (1 << 30) else rms.RMS_SCHEDULE_AUTO)
                 rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_L2_BUDGET, budget)
                 F = torch.full((nlos, cfg.nphi, 2), float("nan"), device=dev)
                 pi = torch.full((nlos,), -7, dtype=torch.int32, device=dev)
@@ -563,6 +565,8 @@ def test_pair_edges(rms, inputs, oracle_mod, nlos):
     with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
         outs = []
         for budget, with_f in ((1 << 40, True), (1 << 20, True), (1 << 20, False)):
+            rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_SCHEDULE,
+                                    rms.RMS_SCHEDULE_WHOLE if budget > (1 << 30) else rms.RMS_SCHEDULE_AUTO)
             rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_L2_BUDGET, budget)
             F = torch.full((nlos, len(phi), 2), float("nan"), device=dev) if with_f else None
             pi = torch.full((nlos,), -7, dtype=torch.int32, device=dev)
