@@ -557,8 +557,9 @@ rms_status rms_synth_window(rms_window_t win, const float *Q, const float *U, in
  * may be NULL): phi_peak, peak_abs [nlos] floats (as rms_synth; from the
  * window or the full grid); fallback [nlos] int32, 1 where the full grid was
  * used; nfallback: device int64, the number of fallbacks.  net and win must
- * belong to the same plan.  Asynchronous; per-call scratch as rms_synth plus
- * 20 bytes per LOS.
+ * belong to the same plan.  Asynchronous; per-call scratch from the stream-
+ * ordered pool: two split operand images (as rms_synth's, the second for the
+ * fallback rows), 2 x hidden bytes of activations and 44 bytes per LOS.
  */
 rms_status rms_peakmap_learned(rms_window_t win, rms_net_t net, const float *Q, const float *U, int64_t nlos,
                                int32_t layout, float tau, float *phi_peak, float *peak_abs, int32_t *fallback,

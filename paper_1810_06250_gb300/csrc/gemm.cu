@@ -445,12 +445,12 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
     tc_fence_after();
     const uint32_t tmem_base = *S.tmem_slot;
 
-    // Tiles of up to 256 phase rows (HALF > kHalf): each epilogue thread keeps HALF FP32
-    // sums, so warpgroup 0 (producer, MMA issuer) hands registers to the two epilogue
-    // warpgroups at the top of their branches; the shares add up to the launch's
-    // 384 x 168 registers (checked on the host before the first launch).
+    // Each epilogue thread keeps HALF FP32 sums plus four rows' peaks, so (except in
+    // the window variant) warpgroup 0 (producer, MMA issuer) hands registers to the
+    // two epilogue warpgroups at the top of their branches; the shares add up to the
+    // launch's 384 x 168 registers (checked on the host before the first launch).
     if (warp < 4) {
-    if constexpr (HALF > kHalf) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
+    if constexpr (!ROT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
@@ -691,161 +691,337 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 }
         }
     } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kNumEpiWarps) {
-        if constexpr (HALF > kHalf) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
-        // ------------------------------------------------------------ epilogue
-        const int q = warp & 3;
-        const int h = (warp - kEpiWarp0) >> 2;
-        float *stg = S.epi + (warp - kEpiWarp0) * 32 * kEpiLd;
-        const int64_t row_pitch = 2 * (int64_t)P.nphi;
-        uint32_t tph = 0;
-        int g_all = 0, mt_count = 0;
-        bool ok = true;
-        float master[HALF];
-        // the even CTA's barrier that releases a TMEM partial (this CTA's own without pairs)
-        uint32_t tempty_addr[2];
-        for (int b = 0; b < 2; ++b)
-            tempty_addr[b] = PAIR ? mapa_shared(smem_u32(&S.tempty[b]), 0u) : smem_u32(&S.tempty[b]);
-        for (int64_t j = it0; j < njobs && ok; j += istride, ++mt_count) {
-            int64_t it;
-            int nt0, nt1;
-            job_of(P, nit, j, it, nt0, nt1);
-            const int64_t mt = PAIR ? 2 * it + rank : it;
-            const int64_t row = mt * kTileM + 32 * q + lane;
-            float scale = P.out_scale;
-            if (P.rexp != nullptr && row < nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
-            float bm = -1.0f, br = 0.f, bim = 0.f;
-            int bi = INT_MAX;
-            for (int nt = nt0; nt < nt1 && ok; ++nt) {
-                for (int g = 0; g < ngroups; ++g, ++g_all) {
-                    const int b = g_all & 1;
-                    if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) {
-                        ok = false;
-                        break;
+        if constexpr (!ROT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
+        if constexpr (!ROT) {
+            // ------------------------------------------------------------ epilogue
+            // 16x256b TMEM loads: in each 16-lane block l of the quarter, thread t holds
+            // rows 16 l + t/4 and 16 l + t/4 + 8, complex column 4 g + t % 4 of every
+            // 8-column group g of its half; F leaves straight from registers (four lanes
+            // write 32 contiguous bytes of a row), and each lane ends up owning one row's
+            // peak after a butterfly over the four lanes of its row group.
+            constexpr int NG = HALF / 8;
+            constexpr int LB = HALF > kHalf ? 2 : 4;   // 8-column loads per TMEM wait
+            const int q = warp & 3;
+            const int h = (warp - kEpiWarp0) >> 2;
+            const int rq = lane >> 2, cq = lane & 3;
+            const int64_t row_pitch = 2 * (int64_t)P.nphi;
+            uint32_t tph = 0;
+            int g_all = 0, mt_count = 0;
+            bool ok = true;
+            float master[2][NG][4];
+            uint32_t tempty_addr[2];
+            for (int b = 0; b < 2; ++b)
+                tempty_addr[b] = PAIR ? mapa_shared(smem_u32(&S.tempty[b]), 0u) : smem_u32(&S.tempty[b]);
+            for (int64_t j = it0; j < njobs && ok; j += istride, ++mt_count) {
+                int64_t it;
+                int nt0, nt1;
+                job_of(P, nit, j, it, nt0, nt1);
+                const int64_t mt = PAIR ? 2 * it + rank : it;
+                // the thread's rows i = 2 l + s: row0 + 16 l + 8 s
+                const int64_t row0 = mt * kTileM + 32 * q + rq;
+                float scale[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t r = row0 + 16 * (i >> 1) + 8 * (i & 1);
+                    scale[i] = P.out_scale;
+                    if (P.rexp != nullptr && r < nlos) scale[i] = ldexpf(scale[i], -(int)P.rexp[r]);
+                }
+                float bm[4], br[4], bim[4];
+                int bi[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { bm[i] = -1.0f; br[i] = 0.f; bim[i] = 0.f; bi[i] = INT_MAX; }
+                for (int nt = nt0; nt < nt1 && ok; ++nt) {
+                    for (int g = 0; g < ngroups; ++g, ++g_all) {
+                        const int b = g_all & 1;
+                        if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tph ^= 1u << b;
+                        tc_fence_after();
+                        const uint32_t taddr =
+                            tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kAccStride + h * HALF);
+#pragma unroll
+                        for (int l = 0; l < 2; ++l)
+#pragma unroll
+                            for (int g0 = 0; g0 < NG; g0 += LB) {
+                                uint32_t r[LB][4];
+#pragma unroll
+                                for (int jj = 0; jj < LB; ++jj)
+                                    if (g0 + jj < NG) tmem_ld16x256(taddr + ((uint32_t)(16 * l) << 16) + 8 * (g0 + jj), r[jj]);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int jj = 0; jj < LB; ++jj)
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e)
+                                        if (g0 + jj < NG) {
+                                            const float v = __uint_as_float(r[jj][e]);
+                                            master[l][g0 + jj][e] = g == 0 ? v : __fadd_rn(master[l][g0 + jj][e], v);
+                                        }
+                            }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) {
+                            if constexpr (PAIR) mbar_arrive_cluster(tempty_addr[b]);
+                            else mbar_arrive(tempty_addr[b]);
+                        }
                     }
-                    tph ^= 1u << b;
-                    tc_fence_after();
-                    const uint32_t taddr =
-                        tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kAccStride + h * HALF);
+                    if (!ok) break;
+                    const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * HALF;
+                    const int kbase = (nt * P.tile_n + h * HALF) >> 1;
 #pragma unroll
-                    for (int c0 = 0; c0 < HALF; c0 += 32) {
-                        uint32_t r[4][8];
+                    for (int l = 0; l < 2; ++l)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (c0 + 8 * j < HALF) tmem_ld8(taddr + c0 + 8 * j, r[j]);
-                        tmem_wait_ld();
+                        for (int gg = 0; gg < NG; ++gg) {
+                            const int k = kbase + 4 * gg + cq;
+                            const bool colok = 2 * (4 * gg + cq) < ncols && k < P.nphi;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-#pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                if (c0 + 8 * j < HALF) {
-                                    const float v = __uint_as_float(r[j][e]);
-                                    master[c0 + 8 * j + e] = g == 0 ? v : __fadd_rn(master[c0 + 8 * j + e], v);
+                            for (int sh = 0; sh < 2; ++sh) {
+                                const int i = 2 * l + sh;
+                                const float fr = master[l][gg][2 * sh] * scale[i];
+                                const float fi = master[l][gg][2 * sh + 1] * scale[i];
+                                if (colok) {
+                                    const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
+                                    if (m2 > bm[i]) { bm[i] = m2; bi[i] = k; br[i] = fr; bim[i] = fi; }
+                                    const int64_t r = row0 + 16 * l + 8 * sh;
+                                    if (P.F != nullptr && r < nlos) {
+                                        const int64_t orow = P.rows ? P.rows[r] : r;
+                                        // streaming store: F is written once and must not push the
+                                        // operands out of L2
+                                        __stcs(reinterpret_cast<float2 *>(P.F + orow * row_pitch + 2 * (int64_t)k),
+                                               make_float2(fr, fi));
+                                    }
                                 }
+                            }
+                        }
+                }
+                if (!ok) break;
+                // the four lanes of a row group hold disjoint columns of the same four rows:
+                // a butterfly leaves every lane with all four rows' peaks (lowest index on ties)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int off = 1; off <= 2; off <<= 1) {
+                        const float om = __shfl_xor_sync(0xffffffffu, bm[i], off);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi[i], off);
+                        const float ore = __shfl_xor_sync(0xffffffffu, br[i], off);
+                        const float oim = __shfl_xor_sync(0xffffffffu, bim[i], off);
+                        if (om > bm[i] || (om == bm[i] && oi < bi[i])) { bm[i] = om; bi[i] = oi; br[i] = ore; bim[i] = oim; }
                     }
-                    tc_fence_before();
+                // lane (rq, cq) now owns row i = cq of its group
+                float pm = bm[0], pre = br[0], pim = bim[0];
+                int pi = bi[0];
+#pragma unroll
+                for (int i = 1; i < 4; ++i)
+                    if (cq == i) { pm = bm[i]; pi = bi[i]; pre = br[i]; pim = bim[i]; }
+                const int rowq = 16 * (cq >> 1) + rq + 8 * (cq & 1);
+                const int64_t prow = mt * kTileM + 32 * q + rowq;
+                // combine the two column halves of each row: half 1 publishes, half 0 writes
+                const int par = mt_count & 1;
+                const uint32_t pbar = smem_u32(&S.pkfull[par * 4 + q]);
+                const uint32_t ebar = smem_u32(&S.pkempty[par * 4 + q]);
+                const uint32_t use_par = (mt_count >> 1) & 1;
+                if (h == 1) {
+                    if (!warp_wait(ebar, use_par ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                    S.pk_m[(par * 4 + q) * 32 + rowq] = pm;
+                    S.pk_i[(par * 4 + q) * 32 + rowq] = pi;
+                    S.pk_re[(par * 4 + q) * 32 + rowq] = pre;
+                    S.pk_im[(par * 4 + q) * 32 + rowq] = pim;
                     __syncwarp();
-                    if (lane == 0) {
-                        if constexpr (PAIR) mbar_arrive_cluster(tempty_addr[b]);
-                        else mbar_arrive(tempty_addr[b]);
+                    if (lane == 0) mbar_arrive(pbar);
+                } else {
+                    if (!warp_wait(pbar, use_par, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                    const float om = S.pk_m[(par * 4 + q) * 32 + rowq];
+                    const int oi = S.pk_i[(par * 4 + q) * 32 + rowq];
+                    const float ore = S.pk_re[(par * 4 + q) * 32 + rowq], oim = S.pk_im[(par * 4 + q) * 32 + rowq];
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ebar);
+                    if (om > pm || (om == pm && oi < pi)) { pm = om; pi = oi; pre = ore; pim = oim; }
+                    if (P.jobs_split) {
+                        // this job's peak of the row: |F|^2 bits (monotonic for values >= 0) above
+                        // the complement of the index, so the largest key is the largest |F|^2
+                        // with the lowest index among equal ones; NaN never gets here
+                        if (prow < nlos && pi != INT_MAX)
+                            atomicMax(P.keys + prow, ((unsigned long long)__float_as_uint(pm) << 32) |
+                                                         (unsigned long long)(0xFFFFFFFFu - (uint32_t)pi));
+                    } else if (prow < nlos) {
+                        const int64_t porow = P.rows ? P.rows[prow] : prow;
+                        const bool found = pi != INT_MAX;
+                        if (P.pidx) P.pidx[porow] = found ? pi : -1;
+                        if (P.pabs) P.pabs[porow] = found ? sqrtf(pm) : __int_as_float(0x7fc00000);
+                        if (P.pphi) P.pphi[porow] = found ? P.phi32[pi] : __int_as_float(0x7fc00000);
+                        if (P.pq) P.pq[porow] = found ? pre : __int_as_float(0x7fc00000);
+                        if (P.pu) P.pu[porow] = found ? pim : __int_as_float(0x7fc00000);
+                        if (P.pchi) {
+                            // chi0 = arg F(phi_peak) / 2 - phi_peak lambda_0^2, reduced to [0, pi)
+                            float c = __int_as_float(0x7fc00000);
+                            if (found) {
+                                double x = 0.5 * atan2((double)pim, (double)pre) - P.phi64[pi] * P.lambda0sq;
+                                x -= M_PI * floor(x / M_PI);
+                                c = (float)x;
+                            }
+                            P.pchi[porow] = c;
+                        }
+                    }
+                }
+            }
+        } else {
+            // ------------------------------------------------------------ epilogue
+            const int q = warp & 3;
+            const int h = (warp - kEpiWarp0) >> 2;
+            float *stg = S.epi + (warp - kEpiWarp0) * 32 * kEpiLd;
+            const int64_t row_pitch = 2 * (int64_t)P.nphi;
+            uint32_t tph = 0;
+            int g_all = 0, mt_count = 0;
+            bool ok = true;
+            float master[HALF];
+            // the even CTA's barrier that releases a TMEM partial (this CTA's own without pairs)
+            uint32_t tempty_addr[2];
+            for (int b = 0; b < 2; ++b)
+                tempty_addr[b] = PAIR ? mapa_shared(smem_u32(&S.tempty[b]), 0u) : smem_u32(&S.tempty[b]);
+            for (int64_t j = it0; j < njobs && ok; j += istride, ++mt_count) {
+                int64_t it;
+                int nt0, nt1;
+                job_of(P, nit, j, it, nt0, nt1);
+                const int64_t mt = PAIR ? 2 * it + rank : it;
+                const int64_t row = mt * kTileM + 32 * q + lane;
+                float scale = P.out_scale;
+                if (P.rexp != nullptr && row < nlos) scale = ldexpf(scale, -(int)P.rexp[row]);
+                float bm = -1.0f, br = 0.f, bim = 0.f;
+                int bi = INT_MAX;
+                for (int nt = nt0; nt < nt1 && ok; ++nt) {
+                    for (int g = 0; g < ngroups; ++g, ++g_all) {
+                        const int b = g_all & 1;
+                        if (!warp_wait(smem_u32(&S.tfull[b]), (tph >> b) & 1, S.abort_flag, P.err, P.timeout_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tph ^= 1u << b;
+                        tc_fence_after();
+                        const uint32_t taddr =
+                            tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kAccStride + h * HALF);
+    #pragma unroll
+                        for (int c0 = 0; c0 < HALF; c0 += 32) {
+                            uint32_t r[4][8];
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (c0 + 8 * j < HALF) tmem_ld8(taddr + c0 + 8 * j, r[j]);
+                            tmem_wait_ld();
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j)
+    #pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    if (c0 + 8 * j < HALF) {
+                                        const float v = __uint_as_float(r[j][e]);
+                                        master[c0 + 8 * j + e] = g == 0 ? v : __fadd_rn(master[c0 + 8 * j + e], v);
+                                    }
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) {
+                            if constexpr (PAIR) mbar_arrive_cluster(tempty_addr[b]);
+                            else mbar_arrive(tempty_addr[b]);
+                        }
+                    }
+                    if (!ok) break;
+                    const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * HALF;
+                    const int kbase = (nt * P.tile_n + h * HALF) >> 1;
+    #pragma unroll
+                    for (int p = 0; p < HALF / 2; ++p) {
+                        const float fr = master[2 * p] * scale, fi = master[2 * p + 1] * scale;
+                        master[2 * p] = fr;
+                        master[2 * p + 1] = fi;
+                        const int k = kbase + p;
+                        if (2 * p < ncols && k < P.nphi) {
+                            const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
+                            if (m2 > bm) {
+                                bm = m2;
+                                bi = k;
+                                if constexpr (!ROT) {   // F at the peak (the window kernel has no use for it)
+                                    br = fr;
+                                    bim = fi;
+                                }
+                            }
+                        }
+                    }
+                    if (P.F != nullptr) {
+    #pragma unroll
+                        for (int c0 = 0; c0 < HALF; c0 += kEpiCols) {
+    #pragma unroll
+                            for (int j = 0; j < kEpiCols; ++j)
+                                if (c0 + j < HALF) stg[lane * kEpiLd + j] = master[c0 + j];
+                            __syncwarp();
+                            // 4 lanes per row (one complex each), 8 rows per store instruction
+                            const int jj = (lane & 3) * 2;
+                            const int kk = kbase + (c0 >> 1) + (lane & 3);
+                            const bool colok = c0 + jj < min(ncols, HALF) && kk < P.nphi;
+    #pragma unroll
+                            for (int it = 0; it < 4; ++it) {
+                                const int r = 8 * it + (lane >> 2);
+                                const int64_t grow = mt * kTileM + 32 * q + r;
+                                if (colok && grow < nlos) {
+                                    const int64_t orow = P.rows ? P.rows[grow] : grow;
+                                    const float2 val = make_float2(stg[r * kEpiLd + jj], stg[r * kEpiLd + jj + 1]);
+                                    // streaming store: F is written once and must not push the
+                                    // operands out of L2
+                                    __stcs(reinterpret_cast<float2 *>(P.F + orow * row_pitch + 2 * (int64_t)kk), val);
+                                }
+                            }
+                            __syncwarp();
+                        }
                     }
                 }
                 if (!ok) break;
-                const int ncols = ((nt == P.ntiles_n - 1) ? P.tile_n_last : P.tile_n) - h * HALF;
-                const int kbase = (nt * P.tile_n + h * HALF) >> 1;
-#pragma unroll
-                for (int p = 0; p < HALF / 2; ++p) {
-                    const float fr = master[2 * p] * scale, fi = master[2 * p + 1] * scale;
-                    master[2 * p] = fr;
-                    master[2 * p + 1] = fi;
-                    const int k = kbase + p;
-                    if (2 * p < ncols && k < P.nphi) {
-                        const float m2 = __fadd_rn(__fmul_rn(fr, fr), __fmul_rn(fi, fi));
-                        if (m2 > bm) {
-                            bm = m2;
-                            bi = k;
-                            if constexpr (!ROT) {   // F at the peak (the window kernel has no use for it)
-                                br = fr;
-                                bim = fi;
+                // combine the two column halves of each row: half 1 publishes, half 0 writes
+                const int par = mt_count & 1;
+                const uint32_t pbar = smem_u32(&S.pkfull[par * 4 + q]);
+                const uint32_t ebar = smem_u32(&S.pkempty[par * 4 + q]);
+                const uint32_t use_par = (mt_count >> 1) & 1;
+                if (h == 1) {
+                    if (!warp_wait(ebar, use_par ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                    S.pk_m[(par * 4 + q) * 32 + lane] = bm;
+                    S.pk_i[(par * 4 + q) * 32 + lane] = bi;
+                    S.pk_re[(par * 4 + q) * 32 + lane] = br;
+                    S.pk_im[(par * 4 + q) * 32 + lane] = bim;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(pbar);
+                } else {
+                    if (!warp_wait(pbar, use_par, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
+                    const float om = S.pk_m[(par * 4 + q) * 32 + lane];
+                    const int oi = S.pk_i[(par * 4 + q) * 32 + lane];
+                    const float ore = S.pk_re[(par * 4 + q) * 32 + lane], oim = S.pk_im[(par * 4 + q) * 32 + lane];
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ebar);
+                    if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; br = ore; bim = oim; }
+                    if (P.jobs_split) {
+                        // this job's peak of the row: |F|^2 bits (monotonic for values >= 0) above
+                        // the complement of the index, so the largest key is the largest |F|^2
+                        // with the lowest index among equal ones; NaN never gets here
+                        if (row < nlos && bi != INT_MAX)
+                            atomicMax(P.keys + row, ((unsigned long long)__float_as_uint(bm) << 32) |
+                                                        (unsigned long long)(0xFFFFFFFFu - (uint32_t)bi));
+                    } else if (row < nlos) {
+                        const int64_t orow = P.rows ? P.rows[row] : row;
+                        const bool found = bi != INT_MAX;
+                        if (P.pidx) P.pidx[orow] = found ? bi : -1;
+                        if (P.pabs) P.pabs[orow] = found ? sqrtf(bm) : __int_as_float(0x7fc00000);
+                        if (P.pphi) P.pphi[orow] = found ? P.phi32[bi] : __int_as_float(0x7fc00000);
+                        if (P.pq) P.pq[orow] = found ? br : __int_as_float(0x7fc00000);
+                        if (P.pu) P.pu[orow] = found ? bim : __int_as_float(0x7fc00000);
+                        if (P.pchi) {
+                            // chi0 = arg F(phi_peak) / 2 - phi_peak lambda_0^2, reduced to [0, pi)
+                            float c = __int_as_float(0x7fc00000);
+                            if (found) {
+                                double x = 0.5 * atan2((double)bim, (double)br) - P.phi64[bi] * P.lambda0sq;
+                                x -= M_PI * floor(x / M_PI);
+                                c = (float)x;
                             }
+                            P.pchi[orow] = c;
                         }
-                    }
-                }
-                if (P.F != nullptr) {
-#pragma unroll
-                    for (int c0 = 0; c0 < HALF; c0 += kEpiCols) {
-#pragma unroll
-                        for (int j = 0; j < kEpiCols; ++j)
-                            if (c0 + j < HALF) stg[lane * kEpiLd + j] = master[c0 + j];
-                        __syncwarp();
-                        // 4 lanes per row (one complex each), 8 rows per store instruction
-                        const int jj = (lane & 3) * 2;
-                        const int kk = kbase + (c0 >> 1) + (lane & 3);
-                        const bool colok = c0 + jj < min(ncols, HALF) && kk < P.nphi;
-#pragma unroll
-                        for (int it = 0; it < 4; ++it) {
-                            const int r = 8 * it + (lane >> 2);
-                            const int64_t grow = mt * kTileM + 32 * q + r;
-                            if (colok && grow < nlos) {
-                                const int64_t orow = P.rows ? P.rows[grow] : grow;
-                                const float2 val = make_float2(stg[r * kEpiLd + jj], stg[r * kEpiLd + jj + 1]);
-                                // streaming store: F is written once and must not push the
-                                // operands out of L2
-                                __stcs(reinterpret_cast<float2 *>(P.F + orow * row_pitch + 2 * (int64_t)kk), val);
-                            }
-                        }
-                        __syncwarp();
                     }
                 }
             }
-            if (!ok) break;
-            // combine the two column halves of each row: half 1 publishes, half 0 writes
-            const int par = mt_count & 1;
-            const uint32_t pbar = smem_u32(&S.pkfull[par * 4 + q]);
-            const uint32_t ebar = smem_u32(&S.pkempty[par * 4 + q]);
-            const uint32_t use_par = (mt_count >> 1) & 1;
-            if (h == 1) {
-                if (!warp_wait(ebar, use_par ^ 1, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
-                S.pk_m[(par * 4 + q) * 32 + lane] = bm;
-                S.pk_i[(par * 4 + q) * 32 + lane] = bi;
-                S.pk_re[(par * 4 + q) * 32 + lane] = br;
-                S.pk_im[(par * 4 + q) * 32 + lane] = bim;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(pbar);
-            } else {
-                if (!warp_wait(pbar, use_par, S.abort_flag, P.err, P.timeout_ns)) { ok = false; break; }
-                const float om = S.pk_m[(par * 4 + q) * 32 + lane];
-                const int oi = S.pk_i[(par * 4 + q) * 32 + lane];
-                const float ore = S.pk_re[(par * 4 + q) * 32 + lane], oim = S.pk_im[(par * 4 + q) * 32 + lane];
-                __syncwarp();
-                if (lane == 0) mbar_arrive(ebar);
-                if (om > bm || (om == bm && oi < bi)) { bm = om; bi = oi; br = ore; bim = oim; }
-                if (P.jobs_split) {
-                    // this job's peak of the row: |F|^2 bits (monotonic for values >= 0) above
-                    // the complement of the index, so the largest key is the largest |F|^2
-                    // with the lowest index among equal ones; NaN never gets here
-                    if (row < nlos && bi != INT_MAX)
-                        atomicMax(P.keys + row, ((unsigned long long)__float_as_uint(bm) << 32) |
-                                                    (unsigned long long)(0xFFFFFFFFu - (uint32_t)bi));
-                } else if (row < nlos) {
-                    const int64_t orow = P.rows ? P.rows[row] : row;
-                    const bool found = bi != INT_MAX;
-                    if (P.pidx) P.pidx[orow] = found ? bi : -1;
-                    if (P.pabs) P.pabs[orow] = found ? sqrtf(bm) : __int_as_float(0x7fc00000);
-                    if (P.pphi) P.pphi[orow] = found ? P.phi32[bi] : __int_as_float(0x7fc00000);
-                    if (P.pq) P.pq[orow] = found ? br : __int_as_float(0x7fc00000);
-                    if (P.pu) P.pu[orow] = found ? bim : __int_as_float(0x7fc00000);
-                    if (P.pchi) {
-                        // chi0 = arg F(phi_peak) / 2 - phi_peak lambda_0^2, reduced to [0, pi)
-                        float c = __int_as_float(0x7fc00000);
-                        if (found) {
-                            double x = 0.5 * atan2((double)bim, (double)br) - P.phi64[bi] * P.lambda0sq;
-                            x -= M_PI * floor(x / M_PI);
-                            c = (float)x;
-                        }
-                        P.pchi[orow] = c;
-                    }
-                }
-            }
+
         }
     }
 
@@ -1058,15 +1234,20 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     int maxunits = pair ? (ctas / 2 > 0 ? ctas / 2 : 1) : ctas;
     using KernelFn = void (*)(GemmParams, CUtensorMap, CUtensorMap, CUtensorMap);
     const KernelFn pair_kern = wide ? gemm_kernel<kHalfWide, false, true> : gemm_kernel<kHalf, false, true>;
-    if (wide) {
-        // the wide variant's setmaxnreg shares add up to 384 x 168 registers: launching it
-        // with any other register count would leave its epilogue warpgroups waiting for
-        // registers, so check the build once
+    if (!rot) {
+        // the setmaxnreg shares of the non-window variants add up to 384 x 168 registers:
+        // launching one with any other register count would leave its epilogue
+        // warpgroups waiting for registers, so check the build once
         static const cudaError_t regs_ok = [] {
-            cudaFuncAttributes fa;
-            cudaError_t e1 = cudaFuncGetAttributes(&fa, gemm_kernel<kHalfWide, false, true>);
-            if (e1 != cudaSuccess) return e1;
-            return fa.numRegs == kRegsLaunch ? cudaSuccess : cudaErrorInvalidConfiguration;
+            const KernelFn ks[3] = {gemm_kernel<kHalf, false, false>, gemm_kernel<kHalf, false, true>,
+                                    gemm_kernel<kHalfWide, false, true>};
+            for (const KernelFn k : ks) {
+                cudaFuncAttributes fa;
+                cudaError_t e1 = cudaFuncGetAttributes(&fa, k);
+                if (e1 != cudaSuccess) return e1;
+                if (fa.numRegs != kRegsLaunch) return cudaErrorInvalidConfiguration;
+            }
+            return cudaSuccess;
         }();
         if (regs_ok != cudaSuccess) return regs_ok;
     }

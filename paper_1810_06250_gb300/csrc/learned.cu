@@ -288,8 +288,8 @@ rms_status rms_peakmap_learned(rms_window_t w, rms_net_t net, const float *Q, co
     const size_t ib = up(split_operand_bytes(p, nlos, layout));
     const size_t n4 = up((size_t)nlos * 4), n8 = up((size_t)nlos * 8);
     const size_t hb = up((size_t)nlos * net->hidden * 2);
-    // image | fallback image | h | rscale | bin | conf | centre | widx | wabs | rows | count
-    const size_t total = 2 * ib + hb + 7 * n4 + n8 + 256;
+    // image | fallback image | h | rscale | bin | conf | centre | widx | wabs | rows | count | peak keys
+    const size_t total = 2 * ib + hb + 7 * n4 + 2 * n8 + 256;
     uint8_t *scr = nullptr;
     cudaError_t e = cudaStreamWaitEvent(s, net->last, 0);
     if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&scr), total, s);
@@ -309,6 +309,8 @@ rms_status rms_peakmap_learned(rms_window_t w, rms_net_t net, const float *Q, co
     float *wabs = reinterpret_cast<float *>(q + 5 * n4);
     int64_t *rows = reinterpret_cast<int64_t *>(q + 7 * n4);
     int64_t *count = reinterpret_cast<int64_t *>(q + 7 * n4 + n8);
+    // the fallback contraction's peak keys (its job schedule and CTA pairs)
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(q + 7 * n4 + n8 + 256);
     const unsigned g256 = (unsigned)((nlos + 255) / 256);
 
     SplitOpts so;
@@ -371,6 +373,7 @@ rms_status rms_peakmap_learned(rms_window_t w, rms_net_t net, const float *Q, co
         go.layout = layout;
         go.pabs = peak_abs;
         go.pphi = phi_peak;
+        go.keys = keys;
         e = launch_gemm(p, go, s);
     }
     if (e == cudaSuccess && nfallback) e = cudaMemcpyAsync(nfallback, count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);

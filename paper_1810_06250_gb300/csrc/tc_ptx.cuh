@@ -165,6 +165,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
                  : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 16 lanes x 8 consecutive 32-bit columns, no wait.  Thread t receives the columns
+// 2 (t % 4) and 2 (t % 4) + 1 of lane t / 4 (r[0], r[1]) and of lane t / 4 + 8
+// (r[2], r[3]), lanes counted from the address's lane: four threads hold 32
+// contiguous bytes of a row, so the row can be stored from registers in whole sectors.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
 
 // ----------------------------------------------------------------------------
 // CTA pairs (cluster of 2; tcgen05 with cta_group::2)
