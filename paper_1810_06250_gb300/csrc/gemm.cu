@@ -12,21 +12,22 @@
 //
 // gemm_kernel: C[l][2k + {0,1}] = sum over K of A[l][.] B[2k + {0,1}][.] with the
 // phase matrix B of phase.cu (see umma.cu for the real form of Eq. Fsum).  A CTA
-// is persistent over 128-row M tiles and runs each M tile's N tiles in order.
-//   warp 0      producer: one bulk copy of the split A stage and TMA of the B hi/lo
-//               tiles per stage                                   -> full
+// is persistent over jobs: a job is one M tile (or M-tile pair) with all of its N
+// tiles (whole schedule), or one (N panel, M tile, N tile) triple dealt
+// round-robin (job schedule, see GemmParams).
+//   warp 0      producer: the split A stage and TMA of the B hi/lo tiles  -> full
 //   warp 1      TMEM allocator, single-thread MMA issuer          -> empty, tfull
-//   warp 2      L2 prefetch of the next M tile's operand
+//   warp 2      L2 prefetch of the next M tile's operand (whole schedule only)
 //   warps 4-11  epilogue: warp w owns TMEM lane quarter w % 4 and column half
 //               (w - 4) / 4; folds partials, scales, peak, stores F  -> tempty
 // The PAIR variant runs on clusters of two CTAs (two SMs) with tcgen05's
 // cta_group::2: every MMA is 256 rows (two M tiles, one per CTA) by tile_n, and
 // each CTA's shared memory holds its own 128 A rows and half of the B tile
 // (tile_n / 2 phase rows), so a stage carries half the phase-matrix bytes of the
-// single-CTA kernel for the same MMA work.  Every CTA loads its own stage and
-// waits for it on its own barrier; in the odd CTA warp 1 relays each filled
-// stage to the even CTA (a cluster-scope arrive), whose warp 1 issues the MMAs
-// once both halves are in.  Commits go to the barriers of both CTAs (multicast),
+// single-CTA kernel for the same MMA work.  Each CTA issues the TMA loads of its
+// own stage, and the cta_group::2 form of the copies signals completion on the
+// even CTA's full barrier, which alone expects both halves' bytes; the even CTA's
+// warp 1 issues the MMAs.  Commits go to the barriers of both CTAs (multicast),
 // and the epilogue warps of both CTAs release a TMEM partial on the even CTA's
 // barrier.
 // MMAs run in groups of up to 16 K blocks into one of two TMEM partials and the
@@ -282,6 +283,7 @@ struct GemmParams {
     const int64_t *count;       // optional device count (<= nlos) of live rows
     const int64_t *rows;        // optional: results of row r go to output row rows[r]
     int32_t kblocks, group;
+    int32_t ksteps_last;        // 16-element MMA steps of the last K block that hold channels (1 or 2)
     int32_t nphi, ntiles_n, tile_n, tile_n_last;
     float *F;
     int32_t *pidx;
@@ -325,7 +327,7 @@ struct GSmem {
     uint32_t stage_bytes;
     float *epi, *pk_m, *pk_re, *pk_im;
     int *pk_i;
-    uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;   // conv: pair relay in PAIR
+    uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;   // conv: rotated stage (ROT)
     uint32_t *tmem_slot;
     volatile int *abort_flag;
     volatile int *mt_started;   // M tiles the producer has started (read by the L2 prefetcher)
@@ -419,7 +421,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         for (int s = 0; s < P.stages; ++s) {
             mbar_init(smem_u32(&S.full[s]), 1);
             mbar_init(smem_u32(&S.empty[s]), 1);
-            mbar_init(smem_u32(&S.conv[s]), PAIR ? 1 : 4);
+            mbar_init(smem_u32(&S.conv[s]), 4);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&S.tfull[b]), 1);
@@ -570,8 +572,11 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                             const uint32_t st = smem_u32(S.ring + (size_t)s * S.stage_bytes);
                             const uint32_t a_hi = st, a_lo = st + kStageA;
                             const uint32_t b_hi = st + a_bytes, b_lo = b_hi + b_bytes;
+                            // a last K block with at most 8 channels is zero past its first step
+                            const int nkk = kb == P.kblocks - 1 ? P.ksteps_last : kKBlock / 16;
 #pragma unroll
                             for (int kk = 0; kk < kKBlock / 16; ++kk) {
+                                if (kk > 0 && kk >= nkk) break;
                                 const uint32_t ko = kk * 32;
                                 const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
                                 if constexpr (PAIR) {
@@ -602,7 +607,7 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             }
             if (!ok) stop_peer();
             if constexpr (PAIR) {
-                // both CTAs wait for this commit before they leave (the odd CTA in its relay)
+                // both CTAs wait for this commit before they leave (the odd CTA in its warp 1)
                 mma_commit_pair_mc(smem_u32(S.mma_done), (uint16_t)3);
                 wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
             } else if (issued) {
@@ -1157,6 +1162,12 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.count = o.count;
     P.rows = o.rows;
     P.kblocks = chan ? p.kblocks : p.kblocks_raw;
+    {
+        // channels in the last K block (active ones for channel-major cubes, every
+        // channel for LOS-major ones); 8 or fewer leave its second MMA step all zero
+        const int last = (chan ? p.nact : p.nchan) - kChanPerKBlock * (P.kblocks - 1);
+        P.ksteps_last = last > kChanPerKBlock / 2 ? kKBlock / 16 : 1;
+    }
     // K blocks chained into one TMEM partial before the round-to-nearest fold: the
     // tensor core's accumulation error grows ~4e-8 per chained MMA, which matters for
     // the split precisions only; plain BF16 (error ~1e-3) folds once per N tile.
