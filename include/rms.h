@@ -35,7 +35,8 @@
  *                                  accumulation error: per LOS on the 1536-channel
  *                                  MWA cube, BF16X3 4.6e-6 at 16 and 6.1e-6 at 32);
  *      RMS_GEMM_CTAS (1..SMs)      persistent CTAs of the contraction;
- *      RMS_L2_PREFETCH=1           L2 prefetch of the next M tile (single CTAs, whole schedule);
+ *      RMS_L2_PREFETCH=1           L2 prefetch of the next job's operand (slower on every
+ *                                  cube measured: off by default);
  *      RMS_HOST_CHUNK (>= 1024)    LOS per chunk of rms_synth_host.
  *  - A plan may be used from several streams.  The tensor-core precisions keep
  *    a per-plan scratch for split operands, so every synthesis call on a plan

@@ -17,7 +17,7 @@
 // round-robin (job schedule, see GemmParams).
 //   warp 0      producer: the split A stage and TMA of the B hi/lo tiles  -> full
 //   warp 1      TMEM allocator, single-thread MMA issuer          -> empty, tfull
-//   warp 2      L2 prefetch of the next M tile's operand (whole schedule only)
+//   warp 2      L2 prefetch of the next job's operand (RMS_L2_PREFETCH)
 //   warps 4-11  epilogue: warp w owns TMEM lane quarter w % 4 and column half
 //               (w - 4) / 4; folds partials, scales, peak, stores F  -> tempty
 // The PAIR variant runs on clusters of two CTAs (two SMs) with tcgen05's
@@ -76,6 +76,7 @@ struct SplitParams {
     const int64_t *rows;        // optional: output row r reads cube row rows[r]
     const int64_t *count;       // optional device count: rows >= *count are left as padding
     int32_t nchan, layout, nk, kblocks, mode;
+    int32_t kpg;                // K blocks per CTA: blockIdx.y covers K blocks [y kpg, (y + 1) kpg)
     int32_t vec4;               // LOS-major rows are 16-byte aligned: vector loads
     const int32_t *active;      // channel-major: active channel list
     const uint16_t *kbmask;     // LOS-major: per K block, bit i = channel 16 kb + i active
@@ -143,6 +144,8 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
     const bool valid = row < n_eff;
     const int64_t src = valid ? (P.rows ? P.rows[row] : row) : 0;
     const int sw = (m >> 1) & 3;
+    // this CTA's K blocks (all of them whenever a whole-row pass is needed: FP16X3, rscale)
+    const int kb0 = (int)blockIdx.y * P.kpg, kb1 = min(P.kblocks, kb0 + P.kpg);
     float scale = 1.0f;
     if (P.mode == MODE_FP16X3) {
         // the row's largest |value| sets its power-of-two scale: a first pass
@@ -184,8 +187,8 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
         }
     };
     if (!PAIRS) {
-        uint8_t *dst = dst0;
-        for (int kb = 0; kb < P.kblocks; ++kb, dst += 2 * kStageA) {
+        uint8_t *dst = dst0 + (size_t)kb0 * (2 * kStageA);
+        for (int kb = kb0; kb < kb1; ++kb, dst += 2 * kStageA) {
             float q[16], u[16];
             load_kblock(P, src, valid, kb, q, u);
             if (P.rscale) {
@@ -208,8 +211,8 @@ __global__ void __launch_bounds__(128) split_kernel(const SplitParams P)
             }
         }
     } else {
-        for (int kb = 0; kb < P.kblocks;) {
-            if (valid && kb + 1 < P.kblocks && (kb + 2) * kChanPerKBlock <= P.nchan) {
+        for (int kb = kb0; kb < kb1;) {
+            if (valid && kb + 1 < kb1 && (kb + 2) * kChanPerKBlock <= P.nchan) {
                 // two K blocks at once: 128 contiguous bytes of the row per array, whole lines
                 const int c0 = kb * kChanPerKBlock;
                 const uint32_t live = __ldg(P.kbmask + kb) | ((uint32_t)__ldg(P.kbmask + kb + 1) << 16);
@@ -307,7 +310,7 @@ struct GemmParams {
     int32_t jobs_split, npanels;
     unsigned long long *keys;
     int32_t b_rows;             // phase rows of a B stage in this CTA's shared memory (tile_n, or tile_n / 2 in pairs)
-    int32_t prefetch;           // L2 prefetch of the next M tile's operand
+    int32_t prefetch;           // L2 prefetch of the next job's operand
     // window rotation (rotating kernel only): row r's operand is multiplied by
     // T[clamp(centre[r], cmin, cmax)][channel] before it enters the MMA
     const int32_t *centre;
@@ -330,7 +333,7 @@ struct GSmem {
     uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;   // conv: rotated stage (ROT)
     uint32_t *tmem_slot;
     volatile int *abort_flag;
-    volatile int *mt_started;   // M tiles the producer has started (read by the L2 prefetcher)
+    volatile int *mt_started;   // jobs the producer has started (read by the L2 prefetcher)
 };
 
 __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
@@ -617,21 +620,25 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         }
     } else if (warp == 2) {
         // ------------------------------------------------------------ L2 prefetcher
-        // When the producer starts an M tile, bring the next M tile's split operand
-        // (one contiguous block) into L2 so its first N tile does not wait on HBM.
-        // A performance hint only: on a stall or an abort it stops.
+        // When the producer starts a job, bring the next job's split operand (this
+        // CTA's M tile: one contiguous block) into L2, so that its first stages do not
+        // wait on HBM.  A performance hint only: on a stall or an abort it stops.
         const size_t blk = (size_t)P.kblocks * (2 * kStageA);
-        int mt_count = 0;
-        for (int64_t mt = blockIdx.x; !PAIR && P.prefetch && !P.jobs_split && mt + gridDim.x < nmt;
-             mt += gridDim.x, ++mt_count) {
+        int n = 0;
+        for (int64_t j = it0; P.prefetch && j + istride < njobs; j += istride, ++n) {
             const uint64_t t0 = global_ns();
             bool go = true;
-            while (go && *S.mt_started < mt_count + 1) {
+            while (go && *S.mt_started < n + 1) {
                 __nanosleep(256);
                 go = !*S.abort_flag && (int64_t)(global_ns() - t0) < P.timeout_ns / 4;
             }
             if (!__all_sync(0xffffffffu, go)) break;
-            const uint8_t *nxt = P.A + (size_t)(mt + gridDim.x) * blk;
+            int64_t it;
+            int nt0, nt1;
+            job_of(P, nit, j + istride, it, nt0, nt1);
+            const int64_t mt = PAIR ? 2 * it + rank : it;
+            if (mt >= nmt) continue;
+            const uint8_t *nxt = P.A + (size_t)mt * blk;
             for (size_t off = (size_t)lane * 4096; off < blk; off += 32 * 4096)
                 prefetch_l2(nxt + off, (uint32_t)min((size_t)4096, blk - off));
         }
@@ -1143,8 +1150,21 @@ cudaError_t launch_split(const rms_plan_s &p, const SplitOpts &o, cudaStream_t s
     sp.vec4 = !chan && (p.nchan % 4 == 0) && !(reinterpret_cast<uintptr_t>(o.Q) & 15) &&
               !(reinterpret_cast<uintptr_t>(o.U) & 15);
     if (sp.mode == MODE_FP16X3 && !o.rexp) return cudaErrorInvalidValue;
-    if (!chan && sp.vec4) split_kernel<true><<<(unsigned)nmt, 128, 0, s>>>(sp);
-    else split_kernel<false><<<(unsigned)nmt, 128, 0, s>>>(sp);
+    // A grid of one CTA per M tile leaves a partial last wave (the LOFAR cube's 2,048
+    // tiles are 1.5 waves at 9 CTAs per SM), so the K blocks of a tile are shared out
+    // over blockIdx.y until the grid is about 8 waves; FP16X3 (a row's largest value
+    // sets its scale) and rscale (a row's RMS) need the whole row in one thread.
+    int ngroups = 1;
+    if (sp.mode != MODE_FP16X3 && !o.rscale) {
+        const int64_t target = (int64_t)8 * 9 * p.num_sms;
+        ngroups = (int)std::min<int64_t>(sp.kblocks, std::max<int64_t>(1, (target + nmt - 1) / nmt));
+    }
+    sp.kpg = (sp.kblocks + ngroups - 1) / ngroups;
+    if (sp.vec4 && (sp.kpg & 1) && sp.kpg < sp.kblocks) ++sp.kpg;   // LOS-major pairs of K blocks stay whole
+    ngroups = (sp.kblocks + sp.kpg - 1) / sp.kpg;
+    const dim3 grid((unsigned)nmt, (unsigned)ngroups);
+    if (!chan && sp.vec4) split_kernel<true><<<grid, 128, 0, s>>>(sp);
+    else split_kernel<false><<<grid, 128, 0, s>>>(sp);
     return cudaGetLastError();
 }
 
@@ -1201,8 +1221,10 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.ldT = o.ldT;
     P.cmin = o.cmin;
     P.cmax = o.cmax;
-    // RMS_L2_PREFETCH=1 turns on the L2 prefetch of the next M tile's operand (off by
-    // default: on the LOFAR cube it evicted the current M tile's operand and cost 6%)
+    // RMS_L2_PREFETCH=1 turns on the L2 prefetch of the next job's operand (off by
+    // default: the operand streams already arrive in time, and the prefetch's extra L2
+    // traffic cost 5% on the LOFAR cube, 10% on the MWA cube and 16% on the 2048^2 x
+    // 800 x 1001 cube)
     static const int prefetch = [] {
         const char *v = std::getenv("RMS_L2_PREFETCH");
         return (v && v[0] == '1') ? 1 : 0;
