@@ -443,14 +443,15 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
     # end to end through host buffers, right after the device-timed region (before the
     # CPU oracle and the other paths run)
     if with_e2e and in_gb < 32:
-        Qh = torch.empty(q.shape, dtype=torch.float32, pin_memory=True)
-        Uh = torch.empty(u.shape, dtype=torch.float32, pin_memory=True)
+        # page-locked host buffers from the library's allocator (registered huge-page memory)
+        hbufs = [rms.HostBuffer(q.shape), rms.HostBuffer(u.shape)] + \
+                ([] if peak_only else [rms.HostBuffer((L, cfg.nphi, 2))]) + \
+                [rms.HostBuffer(L, "int32"), rms.HostBuffer(L), rms.HostBuffer(L)]
+        Qh, Uh = hbufs[0].tensor, hbufs[1].tensor
+        Fh = None if peak_only else hbufs[2].tensor
+        ih, ah, ph = (b.tensor for b in hbufs[-3:])
         Qh.copy_(q)
         Uh.copy_(u)
-        Fh = None if peak_only else torch.empty(L, cfg.nphi, 2, pin_memory=True)
-        ih = torch.empty(L, dtype=torch.int32, pin_memory=True)
-        ah = torch.empty(L, pin_memory=True)
-        ph = torch.empty(L, pin_memory=True)
 
         def e2e_step():
             plan.synth_host(Qh, Uh, L, layout, Fh, ih, ah, ph, stream)
@@ -464,13 +465,16 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
         dt = sum(per_e2e) / n_e2e
         res["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3, "steps": n_e2e,
                       "ms_median_min_max": [1e3 * statistics.median(per_e2e), 1e3 * min(per_e2e), 1e3 * max(per_e2e)],
-                      "note": "host-link throughput varies with other jobs on the shared host: the same call has "
-                              "measured from 199 to 480 ms per cube",
+                      "note": "the median, minimum and maximum over the calls are beside the mean: host-link "
+                              "throughput varies with what else runs on the host",
                       "h2d_bytes_per_step": int(Qh.numel() * 4 + Uh.numel() * 4),
                       "d2h_bytes_per_step": int((0 if Fh is None else Fh.numel() * 4) + L * 12),
-                      "how": "rms_synth_host: pinned host Q/U -> device in LOS chunks, synthesis, F and peak "
-                             "map -> pinned host, copies overlapped on three streams, sync"}
-        del Qh, Uh, Fh
+                      "how": "rms_synth_host: Q/U in page-locked host buffers from rms_host_alloc -> device in "
+                             "LOS chunks, synthesis, F and peak map -> host buffers, copies overlapped on three "
+                             "streams, sync"}
+        del Qh, Uh, Fh, ih, ah, ph
+        for b in hbufs:
+            b.close()
 
     if with_clean and F is not None and cfg.nphi <= 2048 and tensor_path:
         # RM-CLEAN of the synthesised cube (FP64 Hogbom iterations, one warp per LOS)
@@ -726,12 +730,11 @@ def measure_learned(args, dev, local, rank, world, barrier, steps, warmup):
             "gpu_launches": steps * 9, "clocks": clk.summary()}
     solo = rank == 0 and world == 1 and args.config == "learned"
     if solo and not args.no_e2e:
-        Qh = torch.empty(Q.shape, dtype=torch.float32, pin_memory=True)
-        Uh = torch.empty(U.shape, dtype=torch.float32, pin_memory=True)
+        # page-locked host buffers from the library's allocator (registered huge-page memory)
+        hbufs = [rms.HostBuffer(Q.shape), rms.HostBuffer(U.shape), rms.HostBuffer(L), rms.HostBuffer(L)]
+        Qh, Uh, ph_h, pa_h = (b.tensor for b in hbufs)
         Qh.copy_(Q)
         Uh.copy_(U)
-        ph_h = torch.empty(L, pin_memory=True)
-        pa_h = torch.empty(L, pin_memory=True)
 
         def e2e():
             with torch.cuda.stream(stream):
@@ -742,14 +745,22 @@ def measure_learned(args, dev, local, rank, world, barrier, steps, warmup):
                 pa_h.copy_(pka, non_blocking=True)
             stream.synchronize()
         e2e()
-        n_e2e = 3
-        t0 = time.perf_counter()
+        n_e2e = 5
+        per_e2e = []
         for _ in range(n_e2e):
+            t0 = time.perf_counter()
             e2e()
-        dt = (time.perf_counter() - t0) / n_e2e
-        line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
+            per_e2e.append(time.perf_counter() - t0)
+        dt = sum(per_e2e) / n_e2e
+        line["e2e"] = {"value": units / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3, "steps": n_e2e,
+                       "ms_median_min_max": [1e3 * statistics.median(per_e2e), 1e3 * min(per_e2e),
+                                             1e3 * max(per_e2e)],
                        "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(L * 8),
-                       "how": "pinned host Q/U -> device, rms_peakmap_learned, phi_peak and |F|_peak -> pinned host"}
+                       "how": "Q/U in page-locked host buffers from rms_host_alloc -> device, rms_peakmap_learned, "
+                              "phi_peak and |F|_peak -> host buffers"}
+        del Qh, Uh, ph_h, pa_h
+        for b in hbufs:
+            b.close()
     if solo and not args.no_cpu:
         import oracle
         oracle.build()

@@ -35,8 +35,6 @@
  *                                  accumulation error: per LOS on the 1536-channel
  *                                  MWA cube, BF16X3 4.6e-6 at 16 and 6.1e-6 at 32);
  *      RMS_GEMM_CTAS (1..SMs)      persistent CTAs of the contraction;
- *      RMS_L2_PREFETCH=1           L2 prefetch of the next job's operand (slower on every
- *                                  cube measured: off by default);
  *      RMS_HOST_CHUNK (>= 1024)    LOS per chunk of rms_synth_host.
  *  - A plan may be used from several streams.  The tensor-core precisions keep
  *    a per-plan scratch for split operands, so every synthesis call on a plan
@@ -218,7 +216,7 @@ rms_status rms_refine_peaks(rms_plan_t plan, const float *F, int64_t nlos, const
  * rms_synth from HOST buffers: copies Q and U to the device, synthesises, copies
  * F and the peak map back, and synchronises.  Same arguments as rms_synth with
  * every array a host pointer.  Large cubes are processed in chunks of LOS
- * (LOS-major: max(16384, nlos / 16); channel-major: max(65536, nlos / 4),
+ * (LOS-major: max(16384, nlos / 16); channel-major: max(65536, nlos / 8),
  * whose 2-D copies need long rows) through three device slots, with the
  * copies in on a plan-owned stream, the synthesis on `stream` and the copies
  * out on a second plan-owned stream, so that they overlap; a channel-major
@@ -230,6 +228,26 @@ rms_status rms_refine_peaks(rms_plan_t plan, const float *F, int64_t nlos, const
 rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64_t nlos,
                           int32_t layout, float *F_out, int32_t *peak_idx, float *peak_abs,
                           float *phi_peak, void *stream);
+
+/*
+ * Page-locked host memory for rms_synth_host (the paper streams cubes that live
+ * in host memory through the GPU, Sec. 3.2; this call has no counterpart
+ * there).  rms_host_alloc maps `bytes` of anonymous memory, asks the kernel for
+ * transparent huge pages on it (a hint), and registers it with CUDA
+ * (cudaHostRegister, portable to every device), so that copies to and from it
+ * run at the host link's full rate.  Measured on GB300: once other processes
+ * had used and released host memory, buffers from the CUDA host allocator
+ * (cudaHostAlloc, as behind torch's pin_memory) copied to the device at 72 GB/s,
+ * while registered huge-page memory kept 210 GB/s.
+ *
+ * *ptr receives the address (64 KB aligned or better), or NULL on failure;
+ * the memory is not initialised.  Release it with rms_host_free(ptr, bytes),
+ * passing the same size.  Returns RMS_ERR_INVALID_ARG for bytes <= 0 or a NULL
+ * ptr, RMS_ERR_OOM when the mapping or the registration fails for lack of
+ * memory, RMS_ERR_CUDA for another registration failure.  Thread-safe.
+ */
+rms_status rms_host_alloc(int64_t bytes, void **ptr);
+rms_status rms_host_free(void *ptr, int64_t bytes);
 
 /*
  * rms_synth for FP16X3 plans that allocates nothing.  The paper has no

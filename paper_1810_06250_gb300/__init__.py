@@ -26,7 +26,7 @@ from ._binding import (  # noqa: F401
     rms_selftest_wait_timeout, rms_clean_create, rms_clean_destroy, rms_clean, rms_refine_peaks,
     rms_window_centres, rms_plan_set_option, RMS_OPT_CONTRACTION, RMS_OPT_L2_BUDGET, RMS_OPT_SCHEDULE, RMS_SCHEDULE_AUTO,
     RMS_SCHEDULE_WHOLE, RMS_CONTRACT_AUTO,
-    RMS_CONTRACT_SINGLE, RMS_CONTRACT_PAIR,
+    RMS_CONTRACT_SINGLE, RMS_CONTRACT_PAIR, rms_host_alloc, rms_host_free, HostBuffer,
 )
 
 

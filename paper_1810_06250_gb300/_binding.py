@@ -37,7 +37,8 @@ EXPORTS = ("rms_plan_create", "rms_rmsf", "rms_synth", "rms_synth_host", "rms_sy
            "rms_net_params", "rms_propose", "rms_net_grad", "rms_train_step", "rms_window_create",
            "rms_window_destroy", "rms_synth_window", "rms_peakmap_learned", "rms_plan_set_kernel_timing",
            "rms_plan_kernel_times", "rms_synth_peaks", "rms_selftest_wait_timeout", "rms_clean_create",
-           "rms_clean_destroy", "rms_clean", "rms_refine_peaks", "rms_window_centres", "rms_plan_set_option")
+           "rms_clean_destroy", "rms_clean", "rms_refine_peaks", "rms_window_centres", "rms_plan_set_option",
+           "rms_host_alloc", "rms_host_free")
 (RMS_NET_NPARAMS, RMS_NET_NIN, RMS_NET_HIDDEN, RMS_NET_NBINS, RMS_NET_MAX_BATCH, RMS_NET_STEPS) = range(6)
 RMS_NET_PARAMS, RMS_NET_GRADS = 0, 1
 
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
             "rms_synth": [P, P, P, _i64, _i32, P, P, P, P, P],
             "rms_synth_host": [P, P, P, _i64, _i32, P, P, P, P, P],
             "rms_synth_noalloc": [P, P, P, _i64, _i32, P, P, P, P, P],
+            "rms_host_alloc": [_i64, ctypes.POINTER(P)],
+            "rms_host_free": [P, _i64],
             "rms_plan_sync": [P, P],
             "rms_plan_info": [P, _i32, P],
             "rms_plan_get": [P, _i32, P, _i64],
@@ -242,6 +245,45 @@ def rms_synth_host(plan: int, Q, U, nlos: int, layout, F_out=None, peak_idx=None
                                _hptr(peak_abs, "float32", "peak_abs"), _hptr(phi_peak, "float32", "phi_peak"),
                                _stream(stream))
     _check(st, "rms_synth_host")
+
+
+def rms_host_alloc(nbytes: int) -> int:
+    """Page-locked host memory (huge-page backed where the kernel allows) for rms_synth_host."""
+    p = _c_void_p()
+    _check(load().rms_host_alloc(int(nbytes), ctypes.byref(p)), "rms_host_alloc")
+    return int(p.value)
+
+
+def rms_host_free(ptr: int, nbytes: int):
+    _check(load().rms_host_free(ptr, int(nbytes)), "rms_host_free")
+
+
+class HostBuffer:
+    """A CPU torch tensor over rms_host_alloc memory; the memory is released by close()
+    (or on leaving a with block), after which the tensor must not be used."""
+
+    def __init__(self, shape, dtype="float32"):
+        import torch
+        shape = tuple(int(x) for x in (shape if isinstance(shape, (tuple, list)) else (shape,)))
+        np_dtype = np.dtype(dtype)
+        self.nbytes = max(1, int(np.prod(shape)) * np_dtype.itemsize)
+        self.ptr = rms_host_alloc(self.nbytes)
+        raw = (ctypes.c_uint8 * self.nbytes).from_address(self.ptr)
+        arr = np.frombuffer(raw, dtype=np_dtype, count=int(np.prod(shape))).reshape(shape)
+        self.tensor = torch.from_numpy(arr)
+
+    def close(self):
+        if self.ptr:
+            self.tensor = None
+            rms_host_free(self.ptr, self.nbytes)
+            self.ptr = 0
+
+    def __enter__(self):
+        return self.tensor
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
 
 def rms_plan_sync(plan: int, stream=None):

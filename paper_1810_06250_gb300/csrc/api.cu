@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <new>
 
+#include <sys/mman.h>
+
 #include "rms_internal.h"
 
 namespace {
@@ -660,6 +662,35 @@ rms_status rms_synth_host(rms_plan_t p, const float *Q, const float *U, int64_t 
     if (st != RMS_OK) return st;
     if (e != cudaSuccess) return from_cuda(e);
     return *p->h_err ? RMS_ERR_TIMEOUT : RMS_OK;
+}
+
+rms_status rms_host_alloc(int64_t bytes, void **ptr)
+{
+    if (!ptr) return RMS_ERR_INVALID_ARG;
+    *ptr = nullptr;
+    if (bytes <= 0) return RMS_ERR_INVALID_ARG;
+    void *m = mmap(nullptr, (size_t)bytes, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (m == MAP_FAILED) return RMS_ERR_OOM;
+#ifdef MADV_HUGEPAGE
+    madvise(m, (size_t)bytes, MADV_HUGEPAGE);   // a hint: without huge pages the memory still works
+#endif
+    const cudaError_t e = cudaHostRegister(m, (size_t)bytes, cudaHostRegisterPortable);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        munmap(m, (size_t)bytes);
+        return from_cuda(e);
+    }
+    *ptr = m;
+    return RMS_OK;
+}
+
+rms_status rms_host_free(void *ptr, int64_t bytes)
+{
+    if (!ptr || bytes <= 0) return RMS_ERR_INVALID_ARG;
+    const cudaError_t e = cudaHostUnregister(ptr);
+    if (e != cudaSuccess) cudaGetLastError();
+    if (munmap(ptr, (size_t)bytes) != 0) return RMS_ERR_INVALID_ARG;
+    return e == cudaSuccess ? RMS_OK : RMS_ERR_CUDA;
 }
 
 rms_status rms_plan_sync(rms_plan_t p, void *stream)

@@ -17,7 +17,6 @@
 // round-robin (job schedule, see GemmParams).
 //   warp 0      producer: the split A stage and TMA of the B hi/lo tiles  -> full
 //   warp 1      TMEM allocator, single-thread MMA issuer          -> empty, tfull
-//   warp 2      L2 prefetch of the next job's operand (RMS_L2_PREFETCH)
 //   warps 4-11  epilogue: warp w owns TMEM lane quarter w % 4 and column half
 //               (w - 4) / 4; folds partials, scales, peak, stores F  -> tempty
 // The PAIR variant runs on clusters of two CTAs (two SMs) with tcgen05's
@@ -286,7 +285,6 @@ struct GemmParams {
     const int64_t *count;       // optional device count (<= nlos) of live rows
     const int64_t *rows;        // optional: results of row r go to output row rows[r]
     int32_t kblocks, group;
-    int32_t ksteps_last;        // 16-element MMA steps of the last K block that hold channels (1 or 2)
     int32_t nphi, ntiles_n, tile_n, tile_n_last;
     float *F;
     int32_t *pidx;
@@ -310,7 +308,6 @@ struct GemmParams {
     int32_t jobs_split, npanels;
     unsigned long long *keys;
     int32_t b_rows;             // phase rows of a B stage in this CTA's shared memory (tile_n, or tile_n / 2 in pairs)
-    int32_t prefetch;           // L2 prefetch of the next job's operand
     // window rotation (rotating kernel only): row r's operand is multiplied by
     // T[clamp(centre[r], cmin, cmax)][channel] before it enters the MMA
     const int32_t *centre;
@@ -333,7 +330,6 @@ struct GSmem {
     uint64_t *full, *empty, *conv, *tfull, *tempty, *pkfull, *pkempty, *mma_done;   // conv: rotated stage (ROT)
     uint32_t *tmem_slot;
     volatile int *abort_flag;
-    volatile int *mt_started;   // jobs the producer has started (read by the L2 prefetcher)
 };
 
 __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
@@ -357,7 +353,6 @@ __device__ __forceinline__ GSmem gcarve(uint8_t *base, const GemmParams &P)
     s.mma_done = s.pkempty + 8;
     s.tmem_slot = reinterpret_cast<uint32_t *>(s.mma_done + 1);
     s.abort_flag = reinterpret_cast<volatile int *>(s.tmem_slot + 1);
-    s.mt_started = s.abort_flag + 1;
     return s;
 }
 
@@ -436,7 +431,6 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
         }
         mbar_init(smem_u32(S.mma_done), 1);
         *S.abort_flag = 0;
-        *S.mt_started = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -468,13 +462,11 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
             int s = 0;
             uint32_t ph = 0, pending = 0, pend_par = 0;
             bool ok = true;
-            int mt_count = 0;
-            for (int64_t j = it0; j < njobs && ok; j += istride, ++mt_count) {
+            for (int64_t j = it0; j < njobs && ok; j += istride) {
                 int64_t it;
                 int nt0, nt1;
                 job_of(P, nit, j, it, nt0, nt1);
                 const int64_t mt = PAIR ? 2 * it + rank : it;
-                *S.mt_started = mt_count + 1;
                 const uint8_t *a_mt = P.A + (size_t)mt * P.kblocks * (2 * kStageA);
                 for (int nt = nt0; nt < nt1 && ok; ++nt) {
                     // phase rows of this CTA's part of the tile: all of it, or the pair's half
@@ -575,11 +567,8 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                             const uint32_t st = smem_u32(S.ring + (size_t)s * S.stage_bytes);
                             const uint32_t a_hi = st, a_lo = st + kStageA;
                             const uint32_t b_hi = st + a_bytes, b_lo = b_hi + b_bytes;
-                            // a last K block with at most 8 channels is zero past its first step
-                            const int nkk = kb == P.kblocks - 1 ? P.ksteps_last : kKBlock / 16;
 #pragma unroll
                             for (int kk = 0; kk < kKBlock / 16; ++kk) {
-                                if (kk > 0 && kk >= nkk) break;
                                 const uint32_t ko = kk * 32;
                                 const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
                                 if constexpr (PAIR) {
@@ -617,30 +606,6 @@ gemm_kernel(const __grid_constant__ GemmParams P, const __grid_constant__ CUtens
                 mma_commit(smem_u32(S.mma_done));
                 wait_bounded(smem_u32(S.mma_done), 0, S.abort_flag, P.err, P.timeout_ns, false);
             }
-        }
-    } else if (warp == 2) {
-        // ------------------------------------------------------------ L2 prefetcher
-        // When the producer starts a job, bring the next job's split operand (this
-        // CTA's M tile: one contiguous block) into L2, so that its first stages do not
-        // wait on HBM.  A performance hint only: on a stall or an abort it stops.
-        const size_t blk = (size_t)P.kblocks * (2 * kStageA);
-        int n = 0;
-        for (int64_t j = it0; P.prefetch && j + istride < njobs; j += istride, ++n) {
-            const uint64_t t0 = global_ns();
-            bool go = true;
-            while (go && *S.mt_started < n + 1) {
-                __nanosleep(256);
-                go = !*S.abort_flag && (int64_t)(global_ns() - t0) < P.timeout_ns / 4;
-            }
-            if (!__all_sync(0xffffffffu, go)) break;
-            int64_t it;
-            int nt0, nt1;
-            job_of(P, nit, j + istride, it, nt0, nt1);
-            const int64_t mt = PAIR ? 2 * it + rank : it;
-            if (mt >= nmt) continue;
-            const uint8_t *nxt = P.A + (size_t)mt * blk;
-            for (size_t off = (size_t)lane * 4096; off < blk; off += 32 * 4096)
-                prefetch_l2(nxt + off, (uint32_t)min((size_t)4096, blk - off));
         }
     }
     } else if (ROT && warp >= kConvWarp0) {
@@ -1182,12 +1147,6 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.count = o.count;
     P.rows = o.rows;
     P.kblocks = chan ? p.kblocks : p.kblocks_raw;
-    {
-        // channels in the last K block (active ones for channel-major cubes, every
-        // channel for LOS-major ones); 8 or fewer leave its second MMA step all zero
-        const int last = (chan ? p.nact : p.nchan) - kChanPerKBlock * (P.kblocks - 1);
-        P.ksteps_last = last > kChanPerKBlock / 2 ? kKBlock / 16 : 1;
-    }
     // K blocks chained into one TMEM partial before the round-to-nearest fold: the
     // tensor core's accumulation error grows ~4e-8 per chained MMA, which matters for
     // the split precisions only; plain BF16 (error ~1e-3) folds once per N tile.
@@ -1221,15 +1180,6 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.ldT = o.ldT;
     P.cmin = o.cmin;
     P.cmax = o.cmax;
-    // RMS_L2_PREFETCH=1 turns on the L2 prefetch of the next job's operand (off by
-    // default: the operand streams already arrive in time, and the prefetch's extra L2
-    // traffic cost 5% on the LOFAR cube, 10% on the MWA cube and 16% on the 2048^2 x
-    // 800 x 1001 cube)
-    static const int prefetch = [] {
-        const char *v = std::getenv("RMS_L2_PREFETCH");
-        return (v && v[0] == '1') ? 1 : 0;
-    }();
-    P.prefetch = prefetch;
     // the two-CTA contraction serves full-grid calls unless the plan asks for single
     // CTAs (rms_plan_set_option); in the environment RMS_GEMM_PAIR=0 makes single CTAs
     // the default and RMS_GEMM_PAIR=2 CTA pairs wherever the tiles allow them

@@ -48,6 +48,13 @@ def test_null_plan_is_rejected(lib):
     out = ctypes.c_void_p(1)
     assert lib.rms_plan_create(ctypes.byref(out), None, 4, 1, None, None, 4, 3, 0) == 1
     assert out.value is None
+    # host allocator: sizes and pointers are checked before anything is mapped or registered
+    ptr = ctypes.c_void_p(1)
+    assert lib.rms_host_alloc(ctypes.c_int64(0), ctypes.byref(ptr)) == 1 and ptr.value is None
+    assert lib.rms_host_alloc(ctypes.c_int64(-5), ctypes.byref(ptr)) == 1
+    assert lib.rms_host_alloc(ctypes.c_int64(4096), None) == 1
+    assert lib.rms_host_free(None, ctypes.c_int64(4096)) == 1
+    assert lib.rms_host_free(ctypes.c_void_p(4096), ctypes.c_int64(0)) == 1
 
 
 def test_header_is_plain_c():

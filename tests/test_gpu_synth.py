@@ -335,6 +335,37 @@ def test_synth_host_matches_device(rms, inputs, layout):
         assert torch.equal(i2, i0.cpu())
 
 
+def test_synth_host_from_registered_buffers(rms, inputs):
+    """Host buffers from rms_host_alloc (registered huge-page memory) serve
+    rms_synth_host like any pinned memory: results equal rms_synth's bit for bit;
+    the buffers are released again."""
+    from paper_1810_06250_gb300 import learned as L
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = axes(inputs, cfg)
+    n = 70000                                    # channel-major: 2 chunks of 65536 (the second ragged)
+    with rms.Plan(freq, phi, "bf16x3", weights=w) as plan:
+        q, u = L.generate(plan.handle, cfg, 0, n, "chan")
+        F0 = torch.empty(n, cfg.nphi, 2, device="cuda")
+        i0 = torch.empty(n, dtype=torch.int32, device="cuda")
+        plan.synth(q, u, n, "chan", F0, i0)
+        plan.sync()
+        bufs = [rms.HostBuffer(q.shape), rms.HostBuffer(u.shape), rms.HostBuffer((n, cfg.nphi, 2)),
+                rms.HostBuffer(n, "int32")]
+        try:
+            qh, uh, Fh, ih = (b.tensor for b in bufs)
+            assert qh.data_ptr() % 65536 == 0
+            qh.copy_(q)
+            uh.copy_(u)
+            Fh.fill_(float("nan"))
+            ih.fill_(-7)
+            plan.synth_host(qh, uh, n, "chan", Fh, ih)
+            assert torch.equal(Fh, F0.cpu()) and torch.equal(ih, i0.cpu())
+        finally:
+            for b in bufs:
+                b.close()
+        assert all(b.ptr == 0 for b in bufs)
+
+
 # ------------------------------------------------------------------- Q, U and chi0 at the peak
 @pytest.mark.parametrize("path", ["bf16x3", "fp16x3"])
 @pytest.mark.parametrize("layout", ["chan", "los"])
