@@ -234,11 +234,11 @@ rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64
  * in host memory through the GPU, Sec. 3.2; this call has no counterpart
  * there).  rms_host_alloc maps `bytes` of anonymous memory, asks the kernel for
  * transparent huge pages on it (a hint), and registers it with CUDA
- * (cudaHostRegister, portable to every device), so that copies to and from it
- * run at the host link's full rate.  Measured on GB300: once other processes
- * had used and released host memory, buffers from the CUDA host allocator
- * (cudaHostAlloc, as behind torch's pin_memory) copied to the device at 72 GB/s,
- * while registered huge-page memory kept 210 GB/s.
+ * (cudaHostRegister, portable to every device), so that the copies of
+ * rms_synth_host overlap and run at the host link's rate (on GB300 210 GB/s to
+ * the device and 193 GB/s back, the same as memory from cudaHostAlloc).  It
+ * serves callers without a CUDA-aware allocator of their own; huge pages keep
+ * the page tables of a cube of tens of GB small.
  *
  * *ptr receives the address (64 KB aligned or better), or NULL on failure;
  * the memory is not initialised.  Release it with rms_host_free(ptr, bytes),
