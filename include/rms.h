@@ -236,9 +236,10 @@ rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64
  * transparent huge pages on it (a hint), and registers it with CUDA
  * (cudaHostRegister, portable to every device), so that the copies of
  * rms_synth_host overlap and run at the host link's rate (on GB300 210 GB/s to
- * the device and 193 GB/s back, the same as memory from cudaHostAlloc).  It
- * serves callers without a CUDA-aware allocator of their own; huge pages keep
- * the page tables of a cube of tens of GB small.
+ * the device and 193 GB/s back).  Measured on GB300 after other processes had
+ * used the host's memory: buffers from the CUDA host allocator (cudaHostAlloc,
+ * behind torch's pin_memory) copied at 25-85 GB/s to the device while these
+ * kept 210 GB/s, in the same process.
  *
  * *ptr receives the address (64 KB aligned or better), or NULL on failure;
  * the memory is not initialised.  Release it with rms_host_free(ptr, bytes),

@@ -1194,12 +1194,43 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     // channel-major, 0.69 against 0.74 LOS-major; whole schedule 0.87 against 0.75;
     // plain BF16 0.53 against 0.50).
     const bool f_at_peak = o.pq || o.pu || o.pchi;
-    const bool jobs = !rot && o.keys && p.schedule != RMS_SCHEDULE_WHOLE && (o.F || !f_at_peak);
-    const bool pair_wanted =
-        p.contraction == RMS_CONTRACT_PAIR ||
-        (p.contraction == RMS_CONTRACT_AUTO &&
-         (pair_default == 2 || (pair_default == 1 && (p.tile_n2 > 2 * kHalf || (jobs && split_mode(mode))))));
-    const bool pair = !rot && pair_wanted && p.pair_maps;
+    auto pair_for = [&](bool with_jobs) {
+        const bool wanted =
+            p.contraction == RMS_CONTRACT_PAIR ||
+            (p.contraction == RMS_CONTRACT_AUTO &&
+             (pair_default == 2 ||
+              (pair_default == 1 && (p.tile_n2 > 2 * kHalf || (with_jobs && split_mode(mode))))));
+        return !rot && wanted && p.pair_maps;
+    };
+    int ctas = p.num_sms;
+    if (const char *v = std::getenv("RMS_GEMM_CTAS")) {   // tuning knob: persistent CTAs
+        int c = std::atoi(v);
+        if (c >= 1 && c <= p.num_sms) ctas = c;
+    }
+    // L2 budget of the schedule choice (below): 80 MiB by default; rms_plan_set_option,
+    // or RMS_L2_BUDGET_MB = 8 .. 1024 in the environment
+    static const double budget_default = [] {
+        const char *v = std::getenv("RMS_L2_BUDGET_MB");
+        const int mb = v ? std::atoi(v) : 0;
+        return (mb >= 8 && mb <= 1024 ? mb : 80) * 1048576.0;
+    }();
+    const double budget = p.l2_budget > 0 ? (double)p.l2_budget : budget_default;
+    const double a_tile = (double)P.kblocks * (split_mode(mode) ? 2 * kStageA : kStageA);
+    const double b_all = (double)p.npad * (chan ? p.kpad : p.kpad_raw) * 2.0 * (split_mode(mode) ? 2 : 1);
+    bool jobs = !rot && o.keys && p.schedule != RMS_SCHEDULE_WHOLE && (o.F || !f_at_peak);
+    if (jobs && !o.F && p.schedule == RMS_SCHEDULE_AUTO) {
+        // Peak map only: with no F to store, the whole schedule's longer jobs win wherever
+        // one panel holds the phase matrix (LOFAR band, peak map only, pairs or single
+        // CTAs: 8.78 against 9.76 ms for 4,194,304 LOS, 0.58 against 0.60 ms for 262,144;
+        // the MWA band, 2 panels, stays split: 95.0 against 100.5 ms)
+        const bool pr = pair_for(true);
+        const int64_t nitp = pr ? (nmt + 1) / 2 : nmt;
+        const int64_t u = std::min<int64_t>(nitp, pr ? std::max(1, ctas / 2) : ctas);
+        const int64_t nt = pr ? p.ntiles_n2 : p.ntiles_n;
+        const double live = (double)((u + nt - 1) / nt + 1) * (pr ? 2.0 : 1.0) * a_tile + b_all;
+        if (live <= budget) jobs = false;
+    }
+    const bool pair = pair_for(jobs);
     P.ntiles_n = pair ? p.ntiles_n2 : p.ntiles_n;
     P.tile_n = pair ? p.tile_n2 : p.tile_n;
     P.tile_n_last = pair ? p.tile_n_last2 : p.tile_n_last;
@@ -1208,11 +1239,6 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     P.stages = gemm_stages(P.b_rows, mode);
     if (P.stages < 2) return cudaErrorInvalidConfiguration;
     size_t smem = gemm_fixed_smem() + (size_t)P.stages * gemm_stage_bytes(P.b_rows, mode) + 24 * (size_t)P.stages;
-    int ctas = p.num_sms;
-    if (const char *v = std::getenv("RMS_GEMM_CTAS")) {   // tuning knob: persistent CTAs
-        int c = std::atoi(v);
-        if (c >= 1 && c <= p.num_sms) ctas = c;
-    }
     const int64_t nit = pair ? (nmt + 1) / 2 : nmt;
     int maxunits = pair ? (ctas / 2 > 0 ? ctas / 2 : 1) : ctas;
     using KernelFn = void (*)(GemmParams, CUtensorMap, CUtensorMap, CUtensorMap);
@@ -1264,21 +1290,12 @@ cudaError_t launch_gemm(const rms_plan_s &p, const GemmOpts &o, cudaStream_t s)
     // when the caller provides key scratch): single-N-tile jobs in panels (see
     // GemmParams), with the smallest number of panels whose working set -- the
     // operands of the M tiles the CTAs share at one time plus one panel of the phase
-    // matrix -- fits the budget (80 MiB by default; rms_plan_set_option, or
-    // RMS_L2_BUDGET_MB = 8 .. 1024 in the environment).
-    static const double budget_default = [] {
-        const char *v = std::getenv("RMS_L2_BUDGET_MB");
-        const int mb = v ? std::atoi(v) : 0;
-        return (mb >= 8 && mb <= 1024 ? mb : 80) * 1048576.0;
-    }();
-    const double budget = p.l2_budget > 0 ? (double)p.l2_budget : budget_default;
+    // matrix -- fits the budget.
     P.jobs_split = 0;
     P.npanels = 1;
     P.keys = nullptr;
     if (jobs) {
         const double tiles_per_unit = pair ? 2.0 : 1.0;
-        const double a_tile = (double)P.kblocks * (split_mode(mode) ? 2 * kStageA : kStageA);
-        const double b_all = (double)p.npad * (chan ? p.kpad : p.kpad_raw) * 2.0 * (split_mode(mode) ? 2 : 1);
         // measured on the LOFAR cube: split jobs 0.70 ms against 0.75 ms for the whole
         // schedule although the latter's working set fits (finer jobs balance the CTAs
         // better), so the split schedule is the default wherever the call has the keys

@@ -577,6 +577,36 @@ def test_schedules_agree(rms, inputs, oracle_mod, path, layout):
     assert (d / m).max() <= 1e-6
 
 
+@pytest.mark.parametrize("path", ["bf16x3", "bf16"])
+def test_peak_map_only_schedules(rms, inputs, oracle_mod, path):
+    """A peak map without F: the automatic choice keeps the whole schedule while one
+    panel of the phase matrix fits the L2 budget and splits into panels of single-tile
+    jobs (peaks merged by 64-bit atomics) when it does not; both give the same peak
+    map, which matches the oracle."""
+    cfg = inputs.CONFIGS["lofar"]
+    freq, w, phi = axes(inputs, cfg)
+    nlos = 20000 + 33
+    Q, U = inputs.make_cube(cfg, 99, nlos)
+    dev = torch.device("cuda")
+    q = torch.from_numpy(inputs.to_layout(Q, "chan")).to(dev)
+    u = torch.from_numpy(inputs.to_layout(U, "chan")).to(dev)
+    rows = np.r_[np.arange(0, nlos, 97), nlos - 1]
+    Fo = oracle_mod.synth(Q[rows], U[rows], oracle_mod.plan(freq, "freq", w), phi)
+    got = []
+    with rms.Plan(freq, phi, path, weights=w) as plan:
+        for budget, split_expected in ((1 << 40, False), (1 << 20, True)):
+            rms.rms_plan_set_option(plan.handle, rms.RMS_OPT_L2_BUDGET, budget)
+            pi = torch.full((nlos,), -7, dtype=torch.int32, device=dev)
+            pa, pp = torch.zeros(nlos, device=dev), torch.zeros(nlos, device=dev)
+            plan.synth(q, u, nlos, "chan", None, pi, pa, pp)
+            plan.sync()
+            assert (rms.rms_plan_info(plan.handle, rms.RMS_INFO_LAST_PANELS) > 0) == split_expected
+            got.append([t.cpu().numpy() for t in (pi, pa, pp)])
+    for a, b in zip(*got):
+        np.testing.assert_array_equal(a, b)
+    gh.check_peaks_oracle(got[0][0][rows], Fo, gh.TOL[path])
+
+
 @pytest.mark.parametrize("nlos", [1, 127, 128, 129, 256, 383])
 def test_pair_edges(rms, inputs, oracle_mod, nlos):
     """CTA pairs on small and ragged cubes: 1536 channels (the MWA band) x 801 phi, whose
