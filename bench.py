@@ -177,7 +177,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(cfg, nact, args.layout), "sample_los_per_step": n},
+            "data": "synthetic", "config": workload_config(cfg, nact, args.layout, False, world),
+            "sample_los_per_step": n,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "%d LOS per step of %d" % (n, cfg.nlos)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -205,6 +206,19 @@ def measured_traffic(kernel_src: str, summary: str):
     """DRAM bytes per launch from a committed ncu summary (None when the source changed)."""
     v = profile_value(kernel_src, summary, "traffic_bytes_per_launch")
     return None if v is None else int(v)
+
+
+def workload_config(cfg, nact, layout, peak_only=False, world=1):
+    """The `config` object of a bench line: the workload, identical in both arms."""
+    L = cfg.nlos
+    return {"workload": workload_name(cfg, nact, layout, peak_only), "nlos_per_gpu": L,
+            "nchan": cfg.nchan, "nchan_active": nact, "nphi": cfg.nphi, "layout": layout,
+            "l2": "inputs larger than L2 (%.2f GB in%s per step)"
+                  % (L * cfg.nchan * 8 / 1e9, "" if peak_only else ", %.2f GB out" % (L * cfg.nphi * 8 / 1e9)),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "units_per_step_total_channels": L * cfg.nchan * cfg.nphi,
+            "inputs": "device-generated by the seeded generator's device twin; the CPU sample is "
+                      "regenerated on the host"}
 
 
 def workload_name(cfg, nact, layout, peak_only=False):
@@ -429,14 +443,7 @@ def measure_cube(args, cfg_name, path, layout, steps, warmup, dev, local, world=
     in_gb = L * cfg.nchan * 8 / 1e9
     res = {"value": value, "unit": UNIT, "ms_per_step": tmax / steps, "steps": steps, "warmup": warmup,
            "dtype": path,
-           "config": {"workload": workload_name(cfg, nact, layout, peak_only), "nlos_per_gpu": L,
-                      "nchan": cfg.nchan, "nchan_active": nact, "nphi": cfg.nphi, "layout": layout,
-                      "l2": "inputs larger than L2 (%.2f GB in%s per step)"
-                            % (in_gb, "" if peak_only else ", %.2f GB out" % (L * cfg.nphi * 8 / 1e9)),
-                      "parallelism": "replicas" if world > 1 else "single GPU",
-                      "units_per_step_total_channels": L * cfg.nchan * cfg.nphi,
-                      "inputs": "device-generated by the seeded generator's device twin; the CPU sample is "
-                                "regenerated on the host"},
+           "config": workload_config(cfg, nact, layout, peak_only, world),
            "roofline": roof, "gpu_launches": steps * (sched["kernels_per_step"] if sched else 1), "plan_ms": plan_ms,
            "clocks": clk.summary()}
 
