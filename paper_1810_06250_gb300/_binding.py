@@ -266,6 +266,7 @@ class HostBuffer:
         import torch
         shape = tuple(int(x) for x in (shape if isinstance(shape, (tuple, list)) else (shape,)))
         np_dtype = np.dtype(dtype)
+        self.ptr = 0
         self.nbytes = max(1, int(np.prod(shape)) * np_dtype.itemsize)
         self.ptr = rms_host_alloc(self.nbytes)
         raw = (ctypes.c_uint8 * self.nbytes).from_address(self.ptr)
@@ -277,6 +278,12 @@ class HostBuffer:
             self.tensor = None
             rms_host_free(self.ptr, self.nbytes)
             self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:       # interpreter shutdown: the library may already be gone
+            pass
 
     def __enter__(self):
         return self.tensor
