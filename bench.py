@@ -155,12 +155,16 @@ def run_reference(args):
     nact = int(np.count_nonzero(w))
     # each step = a bounded sample so that the whole run ends within a few minutes; the
     # sample's LOS are generated on the host as they are needed
+    # the oracle deals LOS to its threads 16 at a time: calibrate and sample in whole
+    # rounds of 16 LOS per thread, so that every host core works
     budget = 150.0
-    Q, U = inputs.make_cube(cfg, 0, 32)
+    rnd = 16 * max(1, oracle.num_threads())
+    Q, U = inputs.make_cube(cfg, 0, min(cfg.nlos, rnd))
     t0 = time.perf_counter()
     oracle.synth(Q, U, op, phi)
-    per_los = (time.perf_counter() - t0) / 32
-    n = int(max(16, min(cfg.nlos, budget / max(1, args.steps + args.warmup) / per_los)))
+    per_los = (time.perf_counter() - t0) / len(Q)
+    n = int(budget / max(1, args.steps + args.warmup) / per_los) // rnd * rnd
+    n = int(min(cfg.nlos, max(rnd, n)))
     pool = min(cfg.nlos, 4 * n)
     Q, U = inputs.make_cube(cfg, 0, pool)
     for i in range(args.warmup):
