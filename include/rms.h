@@ -241,7 +241,7 @@ rms_status rms_synth_host(rms_plan_t plan, const float *Q, const float *U, int64
  * behind torch's pin_memory) copied at 25-85 GB/s to the device while these
  * kept 210 GB/s, in the same process.
  *
- * *ptr receives the address (64 KB aligned or better), or NULL on failure;
+ * *ptr receives the address (aligned to the host page size), or NULL on failure;
  * the memory is not initialised.  Release it with rms_host_free(ptr, bytes),
  * passing the same size.  Returns RMS_ERR_INVALID_ARG for bytes <= 0 or a NULL
  * ptr, RMS_ERR_OOM when the mapping or the registration fails for lack of

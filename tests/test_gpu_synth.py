@@ -353,7 +353,7 @@ def test_synth_host_from_registered_buffers(rms, inputs):
                 rms.HostBuffer(n, "int32")]
         try:
             qh, uh, Fh, ih = (b.tensor for b in bufs)
-            assert qh.data_ptr() % 65536 == 0
+            assert qh.data_ptr() % 4096 == 0              # page aligned
             qh.copy_(q)
             uh.copy_(u)
             Fh.fill_(float("nan"))
